@@ -1,0 +1,326 @@
+// api.cu -- host side of the C ABI (include/rdhei.h): validation, workspace layout,
+// descriptor upload and kernel launch order.  No device memory is allocated here.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rdhei.h"
+#include "common.cuh"
+
+namespace rdhei {
+void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st);
+void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
+void launch_enc_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
+void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
+void launch_hide(const Batch& B, bool extract, cudaStream_t st);
+void launch_lmr_side(const Batch& B, cudaStream_t st);
+}  // namespace rdhei
+
+using namespace rdhei;
+
+struct rdhei_plan {
+  std::vector<rdhei_job> jobs;
+  std::vector<ImgDesc> desc;
+  std::vector<uint32_t> tile_prefix, chunk_prefix;
+  std::vector<size_t> stash_off;
+  size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
+         off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_tile_rows = 0,
+         off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, total = 0;
+  uint32_t total_tiles = 0, total_chunks = 0;
+  bool any_lmr = false, general = false;
+  void* ws = nullptr;
+  Batch batch{};
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static int levels_of(int H, int W) {
+  int m = H < W ? H : W, n = 0;
+  while ((2 << n) <= m) n++;
+  return n;
+}
+
+static int validate_job(const rdhei_job& j) {
+  if (j.H < 1 || j.W < 1 || j.H > 65536 || j.W > 65536) return RDHEI_EINVAL;
+  if ((uint64_t)j.H * (uint64_t)j.W > (1ull << 27)) return RDHEI_EINVAL;
+  if (j.variant != RDHEI_EMR && j.variant != RDHEI_LMR) return RDHEI_EINVAL;
+  const int bmax = j.variant == RDHEI_EMR ? 7 : 8;
+  if (j.b != 0 && (j.b < 2 || j.b > bmax)) return RDHEI_EINVAL;
+  if (j.rot_lmin < 0 || j.rot_lmin > 16) return RDHEI_EINVAL;
+  if (!j.info) return RDHEI_EINVAL;
+  if (reinterpret_cast<uintptr_t>(j.info) & 7) return RDHEI_EINVAL;
+  return RDHEI_OK;
+}
+
+static void build_layout(rdhei_plan* p) {
+  const int n = (int)p->jobs.size();
+  size_t off = 0;
+  p->off_err = off;                      // zero region starts with the error word
+  p->off_zero = off;
+  p->off_tickets = off + 16;
+  off = align_up(off + 16 + 8 * 4, 256);
+  p->off_hist = off;
+  off = align_up(off + (size_t)n * 16 * 4, 256);
+  p->off_chunk_status = off;
+  off = align_up(off + (size_t)p->total_chunks * 8, 256);
+  p->off_tile_flags = off;
+  off = align_up(off + (size_t)p->total_tiles * 4, 256);
+  p->zero_bytes = off - p->off_zero;
+  p->off_desc = off;
+  off = align_up(off + (size_t)n * sizeof(ImgDesc), 256);
+  p->off_tile_prefix = off;
+  off = align_up(off + (size_t)(n + 1) * 4, 256);
+  p->off_chunk_prefix = off;
+  off = align_up(off + (size_t)(n + 1) * 4, 256);
+  p->off_tile_rows = off;
+  off = align_up(off + (size_t)p->total_tiles * 128, 256);
+  p->off_subtree = off;
+  off = align_up(off + (size_t)p->total_tiles * SUBTREE_BYTES, 256);
+  p->off_aux = off;
+  off = align_up(off + (size_t)p->total_tiles * AUX_BYTES, 256);
+  p->off_sigma6 = off;
+  off = align_up(off + (size_t)p->total_tiles, 256);
+  p->off_tilemap = off;
+  off = align_up(off + (size_t)p->total_tiles * sizeof(TileMap), 256);
+  p->stash_off.resize(n);
+  for (int i = 0; i < n; i++) {
+    p->stash_off[i] = off;
+    off = align_up(off + (size_t)p->jobs[i].H * p->jobs[i].W, 256);
+  }
+  p->total = off;
+}
+
+extern "C" {
+
+int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
+  if (!out || n < 0 || (n > 0 && !jobs)) return RDHEI_EINVAL;
+  *out = nullptr;
+  rdhei_plan* p = new (std::nothrow) rdhei_plan();
+  if (!p) return RDHEI_EINVAL;
+  p->jobs.assign(jobs, jobs + n);
+  p->desc.resize(n);
+  p->tile_prefix.resize(n + 1);
+  p->chunk_prefix.resize(n + 1);
+  uint64_t tiles = 0, chunks = 0;
+  for (int i = 0; i < n; i++) {
+    const rdhei_job& j = p->jobs[i];
+    int rc = validate_job(j);
+    if (rc) { delete p; return rc; }
+    ImgDesc& d = p->desc[i];
+    std::memset(&d, 0, sizeof(d));
+    d.H = j.H; d.W = j.W; d.variant = j.variant; d.b = j.b;
+    d.nlev = levels_of(j.H, j.W);
+    int lmin = j.rot_lmin > 0 ? j.rot_lmin : (j.variant == RDHEI_EMR ? 1 : 4);
+    if (d.nlev >= 1 && lmin > d.nlev) lmin = d.nlev;
+    d.lmin = j.rot_enable ? lmin : NO_ROTATION;
+    d.tiles_x = (uint32_t)((j.W + TILE - 1) / TILE);
+    d.tiles_y = (uint32_t)((j.H + TILE - 1) / TILE);
+    d.nchunks = (uint32_t)(((uint64_t)j.H * j.W + CHUNK_PX - 1) / CHUNK_PX);
+    d.tile_base = (uint32_t)tiles;
+    d.chunk_base = (uint32_t)chunks;
+    p->tile_prefix[i] = (uint32_t)tiles;
+    p->chunk_prefix[i] = (uint32_t)chunks;
+    tiles += (uint64_t)d.tiles_x * d.tiles_y;
+    chunks += d.nchunks;
+    for (int k = 0; k < 8; k++) {
+      d.k1[k] = (uint32_t)j.k1[4 * k] | ((uint32_t)j.k1[4 * k + 1] << 8) | ((uint32_t)j.k1[4 * k + 2] << 16) |
+                ((uint32_t)j.k1[4 * k + 3] << 24);
+      d.k2[k] = (uint32_t)j.k2[4 * k] | ((uint32_t)j.k2[4 * k + 1] << 8) | ((uint32_t)j.k2[4 * k + 2] << 16) |
+                ((uint32_t)j.k2[4 * k + 3] << 24);
+    }
+    for (int k = 0; k < 3; k++) {
+      d.n1[k] = (uint32_t)j.nonce1[4 * k] | ((uint32_t)j.nonce1[4 * k + 1] << 8) |
+                ((uint32_t)j.nonce1[4 * k + 2] << 16) | ((uint32_t)j.nonce1[4 * k + 3] << 24);
+      d.n2[k] = (uint32_t)j.nonce2[4 * k] | ((uint32_t)j.nonce2[4 * k + 1] << 8) |
+                ((uint32_t)j.nonce2[4 * k + 2] << 16) | ((uint32_t)j.nonce2[4 * k + 3] << 24);
+    }
+    d.src = j.src; d.dst = j.dst; d.map_bits = j.map_bits; d.eta_bits = j.eta_bits;
+    d.side_bits = j.side_bits; d.side_nbits = j.side_nbits;
+    d.payload = j.payload; d.nbits = j.nbits;
+    d.bits_out = j.bits_out; d.max_bits = j.max_bits;
+    d.info = j.info;
+    if (j.variant == RDHEI_LMR) p->any_lmr = true;
+    if (j.W % 64) p->general = true;
+  }
+  if (tiles >= (1ull << 32) || chunks >= (1ull << 32)) { delete p; return RDHEI_EINVAL; }
+  p->tile_prefix[n] = (uint32_t)tiles;
+  p->chunk_prefix[n] = (uint32_t)chunks;
+  p->total_tiles = (uint32_t)tiles;
+  p->total_chunks = (uint32_t)chunks;
+  build_layout(p);
+  *out = p;
+  return RDHEI_OK;
+}
+
+size_t rdhei_plan_workspace_size(const rdhei_plan* p) { return p ? p->total : 0; }
+
+int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
+  if (!p || !ws) return RDHEI_EINVAL;
+  if (ws_bytes < p->total) return RDHEI_ESPACE;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return RDHEI_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* base = reinterpret_cast<uint8_t*>(ws);
+  const int n = (int)p->jobs.size();
+  for (int i = 0; i < n; i++) p->desc[i].stash = base + p->stash_off[i];
+  // one host image of the descriptor region, copied once
+  const size_t lo = p->off_desc, hi = p->off_chunk_prefix + (size_t)(n + 1) * 4;
+  std::vector<uint8_t> host(hi - lo, 0);
+  if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
+  std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host.data() + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
+  if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RDHEI_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
+  p->ws = ws;
+  Batch& B = p->batch;
+  B.desc = reinterpret_cast<const ImgDesc*>(base + p->off_desc);
+  B.tile_prefix = reinterpret_cast<const uint32_t*>(base + p->off_tile_prefix);
+  B.chunk_prefix = reinterpret_cast<const uint32_t*>(base + p->off_chunk_prefix);
+  B.n_images = n;
+  B.total_tiles = p->total_tiles;
+  B.total_chunks = p->total_chunks;
+  B.err = reinterpret_cast<uint32_t*>(base + p->off_err);
+  B.tickets = reinterpret_cast<uint32_t*>(base + p->off_tickets);
+  B.hist_acc = reinterpret_cast<uint32_t*>(base + p->off_hist);
+  B.chunk_status = reinterpret_cast<unsigned long long*>(base + p->off_chunk_status);
+  B.tile_flags = reinterpret_cast<uint32_t*>(base + p->off_tile_flags);
+  B.tile_rows = base + p->off_tile_rows;
+  B.subtree = base + p->off_subtree;
+  B.aux = base + p->off_aux;
+  B.sigma6 = base + p->off_sigma6;
+  B.tilemap = reinterpret_cast<TileMap*>(base + p->off_tilemap);
+  return RDHEI_OK;
+}
+
+static bool aligned4(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 3) == 0; }
+
+static int check_op(const rdhei_plan* p, int op) {
+  for (const rdhei_job& j : p->jobs) {
+    const bool lmr = j.variant == RDHEI_LMR;
+    switch (op) {
+      case RDHEI_OP_LABEL_ENCRYPT:
+        if (!j.src || !j.dst) return RDHEI_EINVAL;
+        if ((j.map_bits && !aligned4(j.map_bits)) || (j.eta_bits && !aligned4(j.eta_bits))) return RDHEI_EINVAL;
+        if (lmr && j.side_nbits && (!j.side_bits || !aligned4(j.side_bits))) return RDHEI_EINVAL;
+        break;
+      case RDHEI_OP_EMBED:
+        if (!j.src || !j.dst) return RDHEI_EINVAL;
+        if (j.nbits && (!j.payload || !aligned4(j.payload))) return RDHEI_EINVAL;
+        if (j.nbits >= (1ull << 30)) return RDHEI_EINVAL;
+        if (lmr && (!j.map_bits || !aligned4(j.map_bits))) return RDHEI_EINVAL;
+        break;
+      case RDHEI_OP_EXTRACT:
+        if (!j.src) return RDHEI_EINVAL;
+        if (j.max_bits && (!j.bits_out || !aligned4(j.bits_out))) return RDHEI_EINVAL;
+        if (lmr && (!j.map_bits || !aligned4(j.map_bits))) return RDHEI_EINVAL;
+        break;
+      case RDHEI_OP_DECRYPT_RECOVER:
+        if (!j.src || !j.dst) return RDHEI_EINVAL;
+        if (lmr && (!j.map_bits || !j.eta_bits || !aligned4(j.map_bits) || !aligned4(j.eta_bits)))
+          return RDHEI_EINVAL;
+        break;
+      case RDHEI_OP_LMR_SET_SIDE:
+        if (!j.dst) return RDHEI_EINVAL;
+        if (j.side_nbits && (!j.side_bits || !aligned4(j.side_bits))) return RDHEI_EINVAL;
+        break;
+      default:
+        return RDHEI_EINVAL;
+    }
+  }
+  return RDHEI_OK;
+}
+
+int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
+  if (!p || !p->ws) return RDHEI_EINVAL;
+  int rc = check_op(p, op);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
+  if (cudaMemsetAsync(base + p->off_zero, 0, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
+  const Batch& B = p->batch;
+  switch (op) {
+    case RDHEI_OP_LABEL_ENCRYPT:
+      // packed-map outputs of images whose rows do not start on a 16-bit boundary are
+      // OR-ed word by word and must start from zero
+      for (const rdhei_job& j : p->jobs) {
+        if (j.W % 16 == 0) continue;
+        const size_t bytes = (((size_t)j.H * j.W + 31) / 32) * 4;
+        if (j.map_bits && cudaMemsetAsync(j.map_bits, 0, bytes, st) != cudaSuccess) return RDHEI_ECUDA;
+        if (j.variant == RDHEI_LMR && j.eta_bits && cudaMemsetAsync(j.eta_bits, 0, bytes, st) != cudaSuccess)
+          return RDHEI_ECUDA;
+      }
+      launch_pass1(B, 0, p->general, st);
+      launch_topmap(B, true, st);
+      launch_enc_pass2(B, p->any_lmr, st);
+      break;
+    case RDHEI_OP_EMBED:
+      launch_hide(B, false, st);
+      break;
+    case RDHEI_OP_EXTRACT:
+      launch_hide(B, true, st);
+      break;
+    case RDHEI_OP_DECRYPT_RECOVER:
+      launch_pass1(B, 1, p->general, st);
+      launch_topmap(B, false, st);
+      launch_dec_pass2(B, p->any_lmr, st);
+      break;
+    case RDHEI_OP_LMR_SET_SIDE:
+      launch_lmr_side(B, st);
+      break;
+  }
+  return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
+}
+
+void rdhei_plan_destroy(rdhei_plan* p) { delete p; }
+
+size_t rdhei_workspace_size(const rdhei_job* jobs, int n) {
+  rdhei_plan* p = nullptr;
+  if (rdhei_plan_create(jobs, n, &p) != RDHEI_OK) return 0;
+  size_t s = p->total;
+  rdhei_plan_destroy(p);
+  return s;
+}
+
+static int run_once(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream, int op) {
+  rdhei_plan* p = nullptr;
+  int rc = rdhei_plan_create(jobs, n, &p);
+  if (rc) return rc;
+  rc = rdhei_plan_upload(p, ws, ws_bytes, stream);
+  if (!rc) rc = rdhei_plan_run(p, op, stream);
+  rdhei_plan_destroy(p);
+  return rc;
+}
+
+int rdhei_label_encrypt(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_LABEL_ENCRYPT);
+}
+int rdhei_embed(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_EMBED);
+}
+int rdhei_extract(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_EXTRACT);
+}
+int rdhei_decrypt_recover(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_DECRYPT_RECOVER);
+}
+int rdhei_lmr_set_side(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_LMR_SET_SIDE);
+}
+
+int rdhei_workspace_status(void* ws, void* stream, int32_t* code) {
+  if (!ws || !code) return RDHEI_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  if (cudaMemcpyAsync(&v, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RDHEI_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;
+  *code = (int32_t)v;
+  return RDHEI_OK;
+}
+
+size_t rdhei_job_size(void) { return sizeof(rdhei_job); }
+size_t rdhei_info_size(void) { return sizeof(rdhei_info); }
+
+const char* rdhei_version(void) { return "rdhei 0.1 sm_103a"; }
+
+}  // extern "C"

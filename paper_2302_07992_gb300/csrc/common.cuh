@@ -1,0 +1,204 @@
+// common.cuh -- device-side descriptors, keystream and small helpers shared by the
+// sm_103a kernels of the multi-MSB replacement RDHEI path (arXiv 2302.07992).
+//
+// Work decomposition used by every kernel:
+//   * images are cut into 64 x 64 tiles (T = 2^6), ragged at the right/bottom edge;
+//     the composed block rotation of Eq. (roration) maps aligned 2^k tiles onto
+//     aligned 2^k tiles, so tile = unit of gather;
+//   * the keystream s (Sec. "Secret key generation") is ChaCha20 (RFC 8439), one
+//     64-byte block per 64-pixel tile row when W is a multiple of 64;
+//   * raster-order scans (payload offsets of Sec. III-A-2) use 4096-pixel chunks with
+//     a decoupled look-back.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rdhei {
+
+constexpr int TILE = 64;                 // tile side (pixels)
+constexpr int TILE_PX = TILE * TILE;
+constexpr int SUBTREE_BYTES = 352;       // packed 2-bit angles of levels 1..6 (342 used)
+constexpr int AUX_BYTES = 512;           // one bit per tile pixel, tile-major
+constexpr int CHUNK_PX = 4096;           // raster chunk of the payload scans
+constexpr int ROWVAL_BYTES = 64;         // per-tile row carries of the recovery scan
+constexpr int NO_ROTATION = 99;          // lmin value that disables every level
+
+// Offsets of the six levels inside a tile's subtree (row-major per level,
+// (64 >> L) x (64 >> L) entries, 2 bits each, entry e at bits 2(e % 4) of byte e / 4).
+__host__ __device__ constexpr int subtree_off(int L) {
+  return L == 1 ? 0 : L == 2 ? 256 : L == 3 ? 320 : L == 4 ? 336 : L == 5 ? 340 : 341;
+}
+
+// Per-image descriptor, built on the host from an rdhei_job plus the workspace layout.
+struct ImgDesc {
+  const uint8_t* src;
+  uint8_t* dst;
+  uint8_t* map_bits;
+  uint8_t* eta_bits;
+  const uint8_t* side_bits;
+  uint64_t side_nbits;
+  const uint8_t* payload;
+  uint64_t nbits;
+  uint8_t* bits_out;
+  uint64_t max_bits;
+  void* info;                 // rdhei_info*
+  uint8_t* stash;             // N_px bytes: keystream (encode) / decrypted image (decode)
+  int32_t H, W, variant, b;   // b: 0 = from info (hider / receiver) or auto (owner)
+  int32_t lmin, nlev;         // effective smallest level (NO_ROTATION = none), n
+  uint32_t tiles_x, tiles_y, tile_base, chunk_base, nchunks;
+  uint32_t k1[8], n1[3], k2[8], n2[3];
+};
+
+// Per-tile map entry written by the top-level pass.
+struct TileMap {
+  uint32_t enc_src;   // encode: for output tile Q, its source tile P
+  uint32_t dec_dst;   // decode: for original tile P, its rotated tile Q
+  uint8_t enc_shi;    // sum of the angles above level 6 enclosing enc_src (mod 4)
+  uint8_t dec_shi;    // the same for P itself
+  uint8_t pad[6];
+};
+
+// Workspace-wide pointers (device addresses), passed by value to every kernel.
+struct Batch {
+  const ImgDesc* desc;
+  const uint32_t* tile_prefix;    // n + 1 entries: first global tile of each image
+  const uint32_t* chunk_prefix;   // n + 1 entries
+  int n_images;
+  uint32_t total_tiles, total_chunks;
+  uint32_t* err;                  // workspace error word
+  uint32_t* tickets;              // 8 dispenser counters (zeroed per call)
+  uint32_t* hist_acc;             // n * 16 counters (zeroed per call)
+  unsigned long long* chunk_status;   // total_chunks (zeroed per call)
+  uint32_t* tile_flags;           // total_tiles (zeroed per call)
+  uint8_t* tile_rows;             // total_tiles * 128: aggregate + inclusive row carries
+  uint8_t* subtree;               // total_tiles * SUBTREE_BYTES
+  uint8_t* aux;                   // total_tiles * AUX_BYTES
+  uint8_t* sigma6;                // total_tiles
+  TileMap* tilemap;               // total_tiles
+};
+
+// Error codes shared with rdhei.h.
+constexpr int ERR_CAPACITY = 2;
+constexpr int ERR_TIMEOUT = 4;
+
+// ------------------------------------------------------------------------------------
+// ChaCha20 block function (RFC 8439 Sec. 2.3), 20 rounds, written for the GPU: the 16
+// state words stay in registers; rotations are funnel shifts.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
+
+#define RDHEI_QR(a, b, c, d)          \
+  a += b; d ^= a; d = rotl32(d, 16);  \
+  c += d; b ^= c; b = rotl32(b, 12);  \
+  a += b; d ^= a; d = rotl32(d, 8);   \
+  c += d; b ^= c; b = rotl32(b, 7);
+
+__device__ __forceinline__ void chacha20_block(const uint32_t key[8], uint32_t counter,
+                                               const uint32_t nonce[3], uint32_t o[16]) {
+  const uint32_t c0 = 0x61707865u, c1 = 0x3320646eu, c2 = 0x79622d32u, c3 = 0x6b206574u;
+  uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = c3;
+  uint32_t x4 = key[0], x5 = key[1], x6 = key[2], x7 = key[3];
+  uint32_t x8 = key[4], x9 = key[5], x10 = key[6], x11 = key[7];
+  uint32_t x12 = counter, x13 = nonce[0], x14 = nonce[1], x15 = nonce[2];
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    RDHEI_QR(x0, x4, x8, x12) RDHEI_QR(x1, x5, x9, x13) RDHEI_QR(x2, x6, x10, x14) RDHEI_QR(x3, x7, x11, x15)
+    RDHEI_QR(x0, x5, x10, x15) RDHEI_QR(x1, x6, x11, x12) RDHEI_QR(x2, x7, x8, x13) RDHEI_QR(x3, x4, x9, x14)
+  }
+  o[0] = x0 + c0; o[1] = x1 + c1; o[2] = x2 + c2; o[3] = x3 + c3;
+  o[4] = x4 + key[0]; o[5] = x5 + key[1]; o[6] = x6 + key[2]; o[7] = x7 + key[3];
+  o[8] = x8 + key[4]; o[9] = x9 + key[5]; o[10] = x10 + key[6]; o[11] = x11 + key[7];
+  o[12] = x12 + counter; o[13] = x13 + nonce[0]; o[14] = x14 + nonce[1]; o[15] = x15 + nonce[2];
+}
+#undef RDHEI_QR
+
+// Keystream byte at absolute stream position p (slow path, one block per call).
+__device__ __forceinline__ uint32_t ks_word_at(const uint32_t key[8], const uint32_t nonce[3], uint64_t word) {
+  uint32_t o[16];
+  chacha20_block(key, (uint32_t)(word >> 4), nonce, o);
+  uint32_t r = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) r = (i == (int)(word & 15)) ? o[i] : r;
+  return r;
+}
+
+// ------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s bound on any device-side wait
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void set_error(uint32_t* err, int code) { atomicCAS(err, 0u, (uint32_t)code); }
+
+// Image index owning global tile / chunk `g` (binary search in a prefix array).
+__device__ __forceinline__ int owner_of(const uint32_t* prefix, int n, uint32_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(prefix + mid) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
+
+// Quarter-turn of one coordinate bit pair (u = row bit, v = column bit) by `a`
+// counter-clockwise turns: one turn maps (u, v) -> (1 - v, u).  Encoded as a 32-bit
+// table: entry (a, u, v) at bits 2 * (4a + 2u + v), value (u' << 1) | v'.
+//   a=0: 00->00 01->01 10->10 11->11
+//   a=1: 00->10 01->00 10->11 11->01
+//   a=2: 00->11 01->10 10->01 11->00
+//   a=3: 00->01 01->11 10->00 11->10
+constexpr uint32_t ROT_FWD_LUT =
+    (0u << 0) | (1u << 2) | (2u << 4) | (3u << 6) |
+    (2u << 8) | (0u << 10) | (3u << 12) | (1u << 14) |
+    (3u << 16) | (2u << 18) | (1u << 20) | (0u << 22) |
+    (1u << 24) | (3u << 26) | (0u << 28) | (2u << 30);
+// inverse turn: (a, u', v') -> (u, v)
+constexpr uint32_t ROT_INV_LUT =
+    (0u << 0) | (1u << 2) | (2u << 4) | (3u << 6) |
+    (1u << 8) | (3u << 10) | (0u << 12) | (2u << 14) |
+    (3u << 16) | (2u << 18) | (1u << 20) | (0u << 22) |
+    (2u << 24) | (0u << 26) | (3u << 28) | (1u << 30);
+
+__host__ __device__ __forceinline__ uint32_t rot_bits(uint32_t lut, uint32_t a, uint32_t uv) {
+  return (lut >> (2u * (((a & 3u) << 2) | uv))) & 3u;
+}
+
+// Up to 32 bits of an MSB-first stream starting at bit `pos`, returned LSB-first
+// (bit c = stream bit pos + c); `nwords` bounds the 32-bit words that may be read.
+__device__ __forceinline__ uint32_t stream_bits32(const uint8_t* s, uint64_t nwords, uint64_t pos) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(s);
+  uint64_t wi = pos >> 5;
+  uint32_t sh = (uint32_t)(pos & 31);
+  uint32_t w0 = wi < nwords ? bswap32(__ldg(w + wi)) : 0u;
+  uint32_t w1 = (sh && wi + 1 < nwords) ? bswap32(__ldg(w + wi + 1)) : 0u;
+  uint32_t msb = sh ? (w0 << sh) | (w1 >> (32 - sh)) : w0;
+  return __brev(msb);
+}
+
+}  // namespace rdhei

@@ -1,0 +1,282 @@
+// pass1.cu -- first pass over every 64 x 64 tile: keystream, rotation angles of the
+// levels inside the tile, label histogram (owner) or decryption (K1 receiver).
+//
+// One thread owns one 64-pixel tile row: it computes the ChaCha20 block(s) covering
+// that row of the keystream s (Sec. "Secret key generation"), so every keystream byte
+// of the image is computed exactly once per call.  Block sums of s give the
+// quarter-turn angles of Eq. (roration) for levels 1..6 (blocks inside the tile);
+// the tile total feeds the levels above (topmap.cu).
+//
+//   owner (MODE_ENC):  stash := s; label histogram of Eqs. (gliding1/2) from I.
+//   K1 receiver (MODE_DEC): stash := I_e' XOR s with the location map bit kept
+//        (EMR: LSB = map, aux plane = LSB of s; LMR: bit 7 = map l, aux = eta).
+#include "common.cuh"
+
+namespace rdhei {
+
+enum { MODE_ENC = 0, MODE_DEC = 1 };
+
+// mod-4 addition of 32 packed 2-bit lanes
+__device__ __forceinline__ uint64_t add4(uint64_t a, uint64_t b) {
+  const uint64_t L = 0x5555555555555555ull;
+  uint64_t lo = (a ^ b) & L;
+  uint64_t c = (a & b & L) << 1;
+  uint64_t hi = (a ^ b ^ c) & ~L;
+  return lo | hi;
+}
+// pairwise (mod 4) sums of adjacent 2-bit lanes, compacted: 2k lanes -> k lanes
+__device__ __forceinline__ uint64_t pair4(uint64_t v) {
+  const uint64_t M = 0x3333333333333333ull;
+  uint64_t s = ((v & M) + ((v >> 2) & M)) & M;        // lane k in nibble k (2 bits used)
+  s = (s | (s >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  s = (s | (s >> 4)) & 0x00FF00FF00FF00FFull;
+  s = (s | (s >> 8)) & 0x0000FFFF0000FFFFull;
+  s = (s | (s >> 16)) & 0x00000000FFFFFFFFull;
+  return s;
+}
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+  uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+  uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+template <int MODE, bool GENERAL>
+__global__ void __launch_bounds__(64) k_pass1(Batch B) {
+  // keystream staging for rows that straddle two ChaCha blocks (W not a multiple of 64)
+  __shared__ uint32_t ks_stage[GENERAL ? 64 : 1][33];
+  __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
+  __shared__ uint64_t l6_part[2];
+  __shared__ uint32_t zero_cnt[2][8];
+
+  const uint32_t g = blockIdx.x;
+  const int img = owner_of(B.tile_prefix, B.n_images, g);
+  const ImgDesc& d = B.desc[img];
+  const uint32_t t_local = g - d.tile_base;
+  const int ty = (int)(t_local / d.tiles_x), tx = (int)(t_local % d.tiles_x);
+  const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
+  const int H = d.H, W = d.W;
+  const int y = ty * TILE + r, x0 = tx * TILE;
+  const bool row_ok = y < H;
+  const int len = row_ok ? min(TILE, W - x0) : 0;
+  const uint64_t base = (uint64_t)y * W + x0;
+
+  for (int i = r; i < SUBTREE_BYTES / 4; i += 64) reinterpret_cast<uint32_t*>(sub)[i] = 0u;
+
+  // ---- keystream of this tile row -------------------------------------------------
+  uint32_t sw[16];
+  const bool aligned = ((base & 63) == 0) && len == TILE;
+  if (len == 0) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) sw[i] = 0u;
+  } else if (aligned || !GENERAL) {
+    chacha20_block(d.k1, (uint32_t)(base >> 6), d.n1, sw);
+  } else {
+    // the row straddles two ChaCha blocks: stage both and pick the 64 bytes
+    uint32_t o[16];
+    const uint64_t b0 = base >> 6;
+    const int off = (int)(base & 63);
+    if (len > 0) {
+      chacha20_block(d.k1, (uint32_t)b0, d.n1, o);
+#pragma unroll
+      for (int i = 0; i < 16; i++) ks_stage[r][i] = o[i];
+      if (off + len > 64) {
+        chacha20_block(d.k1, (uint32_t)(b0 + 1), d.n1, o);
+#pragma unroll
+        for (int i = 0; i < 16; i++) ks_stage[r][16 + i] = o[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; i++) ks_stage[r][16 + i] = 0u;
+      }
+      ks_stage[r][32] = 0u;
+    }
+    const int wsh = off >> 2, bsh = (off & 3) * 8;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      uint32_t v = 0;
+      if (len > 0) {
+        uint32_t lo = ks_stage[r][wsh + i], hi = ks_stage[r][wsh + i + 1];
+        v = bsh ? __funnelshift_r(lo, hi, bsh) : lo;
+      }
+      // clear bytes past the row end
+      int valid = len - 4 * i;
+      if (valid <= 0) v = 0;
+      else if (valid < 4) v &= (1u << (8 * valid)) - 1u;
+      sw[i] = v;
+    }
+  }
+
+  // ---- row data: owner reads I (histogram), receiver reads I_e' -------------------
+  uint32_t px[16];
+  const uint8_t* src = d.src + base;
+  const bool vec = aligned && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+  if (vec) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      uint4 v = __ldg(s4 + q);
+      px[4 * q] = v.x; px[4 * q + 1] = v.y; px[4 * q + 2] = v.z; px[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        int c = 4 * i + k;
+        if (c < len) v |= (uint32_t)__ldg(src + c) << (8 * k);
+      }
+      px[i] = v;
+    }
+  }
+
+  if (MODE == MODE_ENC) {
+    // stash the keystream for the gather pass
+    uint8_t* st = d.stash + base;
+    if (len > 0) {
+      if (vec && ((reinterpret_cast<uintptr_t>(st) & 15) == 0)) {
+        uint4* s4 = reinterpret_cast<uint4*>(st);
+#pragma unroll
+        for (int q = 0; q < 4; q++) s4[q] = make_uint4(sw[4 * q], sw[4 * q + 1], sw[4 * q + 2], sw[4 * q + 3]);
+      } else {
+        for (int c = 0; c < len; c++) st[c] = (uint8_t)(sw[c >> 2] >> (8 * (c & 3)));
+      }
+    }
+    // label histogram: zeros(b) = #pixels whose top b bits equal the left neighbour's
+    // (Eqs. gliding1/2 with the left-neighbour form of the map).  The first image
+    // column has no left neighbour and is never redundant.
+    uint32_t left;
+    if (len > 0) left = x0 > 0 ? (uint32_t)__ldg(src - 1) : ((px[0] & 0xFFu) ^ 0xFFu);
+    else left = 0;
+    uint32_t nz[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) nz[k] = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      uint32_t prev = i == 0 ? (left << 24) : px[i - 1];
+      uint32_t dd = px[i] ^ __funnelshift_l(prev, px[i], 8);
+      int valid = len - 4 * i;                    // bytes past the row end count as "differs"
+      if (valid < 4) dd |= valid <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (8 * valid));
+      uint32_t m = dd & 0x7F7F7F7Fu;
+      nz[0] += __popc(dd & 0x80808080u);                                   // b = 1
+#pragma unroll
+      for (int b = 2; b <= 8; b++) {
+        const uint32_t K = (0x80u - (0x100u >> b)) * 0x01010101u;            // top b bits nonzero
+        nz[b - 1] += __popc(((m + K) | dd) & 0x80808080u);
+      }
+    }
+    // per-row zero counts = valid pixels - nonzero ones; reduce over the CTA
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      // the 64 examined bytes include the padding past the row end, all "differs"
+      uint32_t z = 64u - nz[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+      if (lane == 0) zero_cnt[warp][k] = z;
+    }
+  } else {
+    // K1 receiver: decrypt into the stash, keep the map bit, and record the aux plane
+    uint64_t auxbits = 0;
+    uint8_t* st = d.stash + base;
+    if (d.variant == 0) {
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        uint32_t s = sw[i];
+        px[i] ^= s & 0xFEFEFEFEu;                       // bits 7..1 decrypted, LSB = map l
+        uint32_t nib = ((s & 0x01010101u) * 0x01020408u) >> 24;   // LSB of s, pixel 4i+k -> bit k
+        auxbits |= (uint64_t)(nib & 0xFu) << (4 * i);
+      }
+    } else {
+      const uint64_t nw = ((uint64_t)H * W + 31) >> 5;
+      uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, base) : 0u;
+      uint32_t lb1 = len > 32 ? stream_bits32(d.map_bits, nw, base + 32) : 0u;
+      uint32_t eb0 = len > 0 ? stream_bits32(d.eta_bits, nw, base) : 0u;
+      uint32_t eb1 = len > 32 ? stream_bits32(d.eta_bits, nw, base + 32) : 0u;
+      uint64_t lb = ((uint64_t)lb1 << 32) | lb0, eb = ((uint64_t)eb1 << 32) | eb0;
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        uint32_t nib = (uint32_t)(lb >> (4 * i)) & 0xFu;
+        uint32_t lbytes = ((nib * 0x00204081u) & 0x01010101u) << 7;
+        px[i] = ((px[i] ^ sw[i]) & 0x7F7F7F7Fu) | lbytes;   // bits 6..0 decrypted, bit 7 = map l
+      }
+      auxbits = eb;
+    }
+    if (len < 64) auxbits &= len > 0 ? ((len == 64) ? ~0ull : ((1ull << len) - 1)) : 0ull;
+    if (len > 0) {
+      if (vec && ((reinterpret_cast<uintptr_t>(st) & 15) == 0)) {
+        uint4* s4 = reinterpret_cast<uint4*>(st);
+#pragma unroll
+        for (int q = 0; q < 4; q++) s4[q] = make_uint4(px[4 * q], px[4 * q + 1], px[4 * q + 2], px[4 * q + 3]);
+      } else {
+        for (int c = 0; c < len; c++) st[c] = (uint8_t)(px[c >> 2] >> (8 * (c & 3)));
+      }
+    }
+    reinterpret_cast<uint64_t*>(B.aux + (size_t)g * AUX_BYTES)[r] = auxbits;
+  }
+
+  // ---- block sums of s at levels 1..6 -------------------------------------------------
+  // rp: 32 two-bit lanes, lane k = (s(r, 2k) + s(r, 2k+1)) mod 4
+  uint64_t v = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    uint32_t t = sw[i] & 0x03030303u;
+    uint32_t u = t + (t >> 8);                             // byte0: c0+c1, byte2: c2+c3
+    uint32_t f = (u & 3u) | (((u >> 16) & 3u) << 2);
+    v |= (uint64_t)f << (4 * i);
+  }
+  __syncthreads();   // sub[] cleared
+  const int lmin = d.lmin;
+  const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
+  const int cov_cols = W - x0;
+  for (int L = 1; L <= 6; L++) {
+    if (L > 1) v = pair4(v);                               // widen the columns
+    if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
+    else {
+      if (lane == 0) l6_part[warp] = v;
+      __syncthreads();
+      v = add4(l6_part[0], l6_part[1]);
+    }
+    const int nb = TILE >> L;                              // blocks per side at this level
+    const int br = r >> L;
+    if ((r & ((1 << L) - 1)) == 0) {
+      uint64_t ang = v;
+      // angle 0 for levels below lmin and for blocks not entirely inside the image
+      const bool row_cov = (br + 1) * (1 << L) <= cov_rows;
+      int ncol = cov_cols >> L;
+      if (ncol > nb) ncol = nb;
+      if (L < lmin || !row_cov || ncol <= 0) ang = 0;
+      else if (ncol < nb) ang &= (1ull << (2 * ncol)) - 1ull;
+      const int bits = 2 * nb;                             // bits per block row
+      const int off = subtree_off(L) * 8 + br * bits;      // bit offset in sub[]
+      if (bits >= 8) {
+        for (int k = 0; k < bits / 8; k++) sub[(off >> 3) + k] = (uint8_t)(ang >> (8 * k));
+      } else {
+        atomicOr(reinterpret_cast<unsigned int*>(sub) + (off >> 5), (uint32_t)(ang & ((1u << bits) - 1)) << (off & 31));
+      }
+    }
+    if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v & 3u);  // raw tile sum for the top levels
+  }
+  __syncthreads();
+  // subtree to global (352 bytes)
+  {
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sub);
+    uint32_t* g32 = reinterpret_cast<uint32_t*>(B.subtree + (size_t)g * SUBTREE_BYTES);
+    for (int i = r; i < SUBTREE_BYTES / 4; i += 64) g32[i] = s32[i];
+  }
+  if (MODE == MODE_ENC && r < 8) {
+    atomicAdd(B.hist_acc + 16 * img + r, zero_cnt[0][r] + zero_cnt[1][r]);
+  }
+}
+
+// general = some image has W % 64 != 0 or a ragged tile row (rows that straddle blocks)
+void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st) {
+  if (B.total_tiles == 0) return;
+  if (mode == MODE_ENC) {
+    if (general) k_pass1<MODE_ENC, true><<<B.total_tiles, 64, 0, st>>>(B);
+    else k_pass1<MODE_ENC, false><<<B.total_tiles, 64, 0, st>>>(B);
+  } else {
+    if (general) k_pass1<MODE_DEC, true><<<B.total_tiles, 64, 0, st>>>(B);
+    else k_pass1<MODE_DEC, false><<<B.total_tiles, 64, 0, st>>>(B);
+  }
+}
+
+}  // namespace rdhei

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of ``librdhei.so`` (C ABI in ``include/rdhei.h``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  Importing this module loads
+the library and fails loudly if it has not been built (``python -m
+paper_2302_07992_gb300.build``) -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+from . import build as _build
+
+EMR, LMR = 0, 1
+OP_LABEL_ENCRYPT, OP_EMBED, OP_EXTRACT, OP_DECRYPT_RECOVER, OP_LMR_SET_SIDE = 0, 1, 2, 3, 4
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE"}
+
+if not os.path.exists(_build.LIB):
+    raise ImportError(f"{_build.LIB} is missing: build it with `python -m paper_2302_07992_gb300.build` "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+_lib = ctypes.CDLL(_build.LIB)
+
+
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("variant", ctypes.c_int32), ("b", ctypes.c_int32),
+        ("rot_lmin", ctypes.c_int32), ("rot_enable", ctypes.c_int32),
+        ("k1", ctypes.c_uint8 * 32), ("nonce1", ctypes.c_uint8 * 12),
+        ("k2", ctypes.c_uint8 * 32), ("nonce2", ctypes.c_uint8 * 12),
+        ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("map_bits", ctypes.c_void_p),
+        ("eta_bits", ctypes.c_void_p), ("side_bits", ctypes.c_void_p), ("side_nbits", ctypes.c_uint64),
+        ("payload", ctypes.c_void_p), ("nbits", ctypes.c_uint64),
+        ("bits_out", ctypes.c_void_p), ("max_bits", ctypes.c_uint64),
+        ("info", ctypes.c_void_p),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("hist", ctypes.c_uint32 * 9), ("b", ctypes.c_int32), ("capacity", ctypes.c_uint64),
+                ("embedded", ctypes.c_uint64), ("extracted", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+INFO_BYTES = ctypes.sizeof(Info)
+
+_JobP = ctypes.POINTER(Job)
+_lib.rdhei_workspace_size.argtypes = [_JobP, ctypes.c_int]
+_lib.rdhei_workspace_size.restype = ctypes.c_size_t
+for _n in ("rdhei_label_encrypt", "rdhei_embed", "rdhei_extract", "rdhei_decrypt_recover", "rdhei_lmr_set_side"):
+    getattr(_lib, _n).argtypes = [_JobP, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    getattr(_lib, _n).restype = ctypes.c_int
+_lib.rdhei_plan_create.argtypes = [_JobP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+_lib.rdhei_plan_create.restype = ctypes.c_int
+_lib.rdhei_plan_workspace_size.argtypes = [ctypes.c_void_p]
+_lib.rdhei_plan_workspace_size.restype = ctypes.c_size_t
+_lib.rdhei_plan_upload.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+_lib.rdhei_plan_upload.restype = ctypes.c_int
+_lib.rdhei_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+_lib.rdhei_plan_run.restype = ctypes.c_int
+_lib.rdhei_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.rdhei_plan_destroy.restype = None
+_lib.rdhei_workspace_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+_lib.rdhei_workspace_status.restype = ctypes.c_int
+_lib.rdhei_job_size.restype = ctypes.c_size_t
+_lib.rdhei_info_size.restype = ctypes.c_size_t
+_lib.rdhei_version.restype = ctypes.c_char_p
+
+assert _lib.rdhei_job_size() == ctypes.sizeof(Job), "rdhei_job layout mismatch"
+assert _lib.rdhei_info_size() == ctypes.sizeof(Info), "rdhei_info layout mismatch"
+
+
+class RdheiError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RdheiError(f"{what} failed: {STATUS.get(rc, rc)}")
+
+
+def version() -> str:
+    return _lib.rdhei_version().decode()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+# ----------------------------------------------------------------------------------
+@dataclass
+class Params:
+    """Per-image method parameters (mirrors the job fields of include/rdhei.h)."""
+    variant: int = EMR
+    b: int = 0
+    rot_lmin: int = 0
+    rot_enable: int = 1
+    k1: bytes = bytes(32)
+    nonce1: bytes = bytes(12)
+    k2: bytes = bytes(32)
+    nonce2: bytes = bytes(12)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def bitbuf(nbits: int, device="cuda") -> torch.Tensor:
+    """Zeroed device buffer for an nbits stream, padded to whole 32-bit words."""
+    return torch.zeros(max(4, ((int(nbits) + 31) // 32) * 4), dtype=torch.uint8, device=device)
+
+
+def as_bitbuf(packed: torch.Tensor, nbits: int) -> torch.Tensor:
+    """Copy an MSB-first packed stream into a word-padded device buffer."""
+    out = bitbuf(nbits, packed.device if packed.is_cuda else "cuda")
+    n = min(packed.numel(), out.numel())
+    out[:n].copy_(packed.reshape(-1)[:n])
+    return out
+
+
+def make_job(p: Params, H: int, W: int, *, src=None, dst=None, map_bits=None, eta_bits=None, side_bits=None,
+             side_nbits=0, payload=None, nbits=0, bits_out=None, max_bits=0, info=None, b=None) -> Job:
+    j = Job()
+    j.H, j.W, j.variant = int(H), int(W), int(p.variant)
+    j.b = int(p.b if b is None else b)
+    j.rot_lmin, j.rot_enable = int(p.rot_lmin), int(p.rot_enable)
+    for name, n in (("k1", 32), ("nonce1", 12), ("k2", 32), ("nonce2", 12)):
+        v = bytes(getattr(p, name))
+        assert len(v) == n, name
+        ctypes.memmove(ctypes.addressof(getattr(j, name)), v, n)
+    j.src, j.dst = _ptr(src), _ptr(dst)
+    j.map_bits, j.eta_bits, j.side_bits = _ptr(map_bits), _ptr(eta_bits), _ptr(side_bits)
+    j.side_nbits = int(side_nbits)
+    j.payload, j.nbits = _ptr(payload), int(nbits)
+    j.bits_out, j.max_bits = _ptr(bits_out), int(max_bits)
+    j.info = _ptr(info)
+    return j
+
+
+def new_info(n: int = 1, device="cuda") -> torch.Tensor:
+    return torch.zeros((n, INFO_BYTES), dtype=torch.uint8, device=device)
+
+
+def read_info(info: torch.Tensor) -> list[dict]:
+    host = info.detach().to("cpu").contiguous()
+    out = []
+    for i in range(host.shape[0]):
+        raw = bytes(host[i].numpy().tobytes())
+        s = Info.from_buffer_copy(raw)
+        out.append({"hist": list(s.hist), "b": s.b, "capacity": s.capacity, "embedded": s.embedded,
+                    "extracted": s.extracted, "status": s.status})
+    return out
+
+
+class Plan:
+    """A validated, uploaded batch: ``run(op)`` launches kernels only (capturable)."""
+
+    def __init__(self, jobs: list[Job], stream=None, workspace: torch.Tensor | None = None):
+        self._jobs = (Job * len(jobs))(*jobs)
+        h = ctypes.c_void_p()
+        _check(_lib.rdhei_plan_create(self._jobs, len(jobs), ctypes.byref(h)), "rdhei_plan_create")
+        self._h = h
+        need = _lib.rdhei_plan_workspace_size(h)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(max(int(need), 256) + 256, dtype=torch.uint8, device="cuda")
+        self.ws = workspace
+        off = (-self.ws.data_ptr()) % 256
+        self._ws_ptr = self.ws.data_ptr() + off
+        self._ws_bytes = self.ws.numel() - off
+        _check(_lib.rdhei_plan_upload(h, ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _stream(stream)),
+               "rdhei_plan_upload")
+
+    def run(self, op: int, stream=None):
+        _check(_lib.rdhei_plan_run(self._h, int(op), _stream(stream)), f"rdhei_plan_run({op})")
+
+    def status(self, stream=None) -> int:
+        code = ctypes.c_int32(0)
+        _check(_lib.rdhei_workspace_status(ctypes.c_void_p(self._ws_ptr), _stream(stream), ctypes.byref(code)),
+               "rdhei_workspace_status")
+        return int(code.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rdhei_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_jobs(op: int, jobs: list[Job], stream=None, check: bool = True) -> int:
+    """One call of the C ABI's named entry point for ``op`` on a batch of jobs."""
+    arr = (Job * len(jobs))(*jobs)
+    need = _lib.rdhei_workspace_size(arr, len(jobs))
+    if need == 0:
+        raise RdheiError("rdhei_workspace_size rejected the jobs")
+    ws = torch.empty(int(need) + 256, dtype=torch.uint8, device="cuda")
+    off = (-ws.data_ptr()) % 256
+    fn = {OP_LABEL_ENCRYPT: _lib.rdhei_label_encrypt, OP_EMBED: _lib.rdhei_embed, OP_EXTRACT: _lib.rdhei_extract,
+          OP_DECRYPT_RECOVER: _lib.rdhei_decrypt_recover, OP_LMR_SET_SIDE: _lib.rdhei_lmr_set_side}[op]
+    st = _stream(stream)
+    _check(fn(arr, len(jobs), ctypes.c_void_p(ws.data_ptr() + off), ws.numel() - off, st), f"op {op}")
+    code = ctypes.c_int32(0)
+    _check(_lib.rdhei_workspace_status(ctypes.c_void_p(ws.data_ptr() + off), st, ctypes.byref(code)),
+           "rdhei_workspace_status")
+    if check and code.value not in (0, 2):
+        raise RdheiError(f"device reported {STATUS.get(code.value, code.value)}")
+    return int(code.value)
+
+
+# ---------------------------------------------------------------- one image --
+def label_encrypt(img: torch.Tensor, p: Params, side_bits: torch.Tensor | None = None, side_nbits: int = 0,
+                  want_maps: bool = True, info: torch.Tensor | None = None, stream=None) -> dict:
+    H, W = img.shape
+    img = img.contiguous()
+    enc = torch.empty_like(img)
+    info = new_info(1) if info is None else info
+    mb = bitbuf(H * W) if want_maps else None
+    eb = bitbuf(H * W) if (want_maps and p.variant == LMR) else None
+    sb = None if side_bits is None else as_bitbuf(side_bits, side_nbits)
+    j = make_job(p, H, W, src=img, dst=enc, map_bits=mb, eta_bits=eb, side_bits=sb, side_nbits=side_nbits,
+                 info=info)
+    run_jobs(OP_LABEL_ENCRYPT, [j], stream)
+    return {"enc": enc, "map_bits": mb, "eta_bits": eb, "info": info, **read_info(info)[0]}
+
+
+def embed(enc: torch.Tensor, p: Params, b: int, payload: torch.Tensor, nbits: int,
+          lmr_map: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None) -> dict:
+    H, W = enc.shape
+    out = torch.empty_like(enc)
+    info = new_info(1) if info is None else info
+    pay = as_bitbuf(payload, nbits)
+    j = make_job(p, H, W, src=enc.contiguous(), dst=out, map_bits=lmr_map, payload=pay, nbits=nbits, info=info, b=b)
+    code = run_jobs(OP_EMBED, [j], stream)
+    return {"marked": out, "status": code, **read_info(info)[0]}
+
+
+def extract(marked: torch.Tensor, p: Params, b: int, max_bits: int, lmr_map: torch.Tensor | None = None,
+            info: torch.Tensor | None = None, stream=None) -> dict:
+    H, W = marked.shape
+    info = new_info(1) if info is None else info
+    out = bitbuf(max_bits)
+    j = make_job(p, H, W, src=marked.contiguous(), map_bits=lmr_map, bits_out=out, max_bits=max_bits, info=info,
+                 b=b)
+    run_jobs(OP_EXTRACT, [j], stream)
+    r = read_info(info)[0]
+    return {"bits": out, **r}
+
+
+def decrypt_recover(marked: torch.Tensor, p: Params, b: int, lmr_map: torch.Tensor | None = None,
+                    lmr_eta: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    H, W = marked.shape
+    info = new_info(1) if info is None else info
+    out = torch.empty_like(marked)
+    j = make_job(p, H, W, src=marked.contiguous(), dst=out, map_bits=lmr_map, eta_bits=lmr_eta, info=info, b=b)
+    run_jobs(OP_DECRYPT_RECOVER, [j], stream)
+    return out
+
+
+def lmr_set_side(enc: torch.Tensor, p: Params, side_bits: torch.Tensor, side_nbits: int, stream=None) -> torch.Tensor:
+    H, W = enc.shape
+    out = enc.clone()
+    info = new_info(1)
+    j = make_job(p, H, W, dst=out, side_bits=as_bitbuf(side_bits, side_nbits), side_nbits=side_nbits, info=info)
+    run_jobs(OP_LMR_SET_SIDE, [j], stream)
+    return out
