@@ -159,6 +159,13 @@ int rdhei_plan_upload(rdhei_plan *plan, void *ws, size_t ws_bytes, void *stream)
 int rdhei_plan_run(rdhei_plan *plan, int op, void *stream);
 void rdhei_plan_destroy(rdhei_plan *plan);
 
+/* The kernels of one operation, one launch per stage, for timing each kernel with
+ * events recorded between stages: stage 0 also issues the per-call workspace memsets.
+ * rdhei_plan_run(plan, op) == every stage of op in order.  Unknown op: 0 stages. */
+int rdhei_plan_stage_count(int op);
+const char *rdhei_stage_name(int op, int stage);
+int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
+
 /* Workspace-wide device error word of the most recent call on this workspace
  * (synchronises the stream).  0 = no error, else an rdhei_status code. */
 int rdhei_workspace_status(void *ws, void *stream, int32_t *code);

@@ -231,16 +231,44 @@ static int check_op(const rdhei_plan* p, int op) {
   return RDHEI_OK;
 }
 
-int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
-  if (!p || !p->ws) return RDHEI_EINVAL;
-  int rc = check_op(p, op);
-  if (rc) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
-  if (cudaMemsetAsync(base + p->off_zero, 0, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
-  const Batch& B = p->batch;
+int rdhei_plan_stage_count(int op) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT:
+    case RDHEI_OP_DECRYPT_RECOVER:
+      return 3;
+    case RDHEI_OP_EMBED:
+    case RDHEI_OP_EXTRACT:
+    case RDHEI_OP_LMR_SET_SIDE:
+      return 1;
+    default:
+      return 0;
+  }
+}
+
+const char* rdhei_stage_name(int op, int stage) {
+  static const char* enc[3] = {"pass1_keystream_hist", "topmap", "enc_gather"};
+  static const char* dec[3] = {"pass1_keystream_decrypt", "topmap", "dec_gather_recover"};
+  switch (op) {
+    case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
+    case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 3 ? dec[stage] : "";
+    case RDHEI_OP_EMBED: return stage == 0 ? "embed_scan" : "";
+    case RDHEI_OP_EXTRACT: return stage == 0 ? "extract_scan" : "";
+    case RDHEI_OP_LMR_SET_SIDE: return stage == 0 ? "lmr_side" : "";
+  }
+  return "";
+}
+
+int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
+  if (!p || !p->ws) return RDHEI_EINVAL;
+  if (stage < 0 || stage >= rdhei_plan_stage_count(op)) return RDHEI_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Batch& B = p->batch;
+  if (stage == 0) {
+    int rc = check_op(p, op);
+    if (rc) return rc;
+    uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
+    if (cudaMemsetAsync(base + p->off_zero, 0, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
+    if (op == RDHEI_OP_LABEL_ENCRYPT) {
       // packed-map outputs of images whose rows do not start on a 16-bit boundary are
       // OR-ed word by word and must start from zero
       for (const rdhei_job& j : p->jobs) {
@@ -250,9 +278,13 @@ int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
         if (j.variant == RDHEI_LMR && j.eta_bits && cudaMemsetAsync(j.eta_bits, 0, bytes, st) != cudaSuccess)
           return RDHEI_ECUDA;
       }
-      launch_pass1(B, 0, p->general, st);
-      launch_topmap(B, true, st);
-      launch_enc_pass2(B, p->any_lmr, st);
+    }
+  }
+  switch (op) {
+    case RDHEI_OP_LABEL_ENCRYPT:
+      if (stage == 0) launch_pass1(B, 0, p->general, st);
+      else if (stage == 1) launch_topmap(B, true, st);
+      else launch_enc_pass2(B, p->any_lmr, st);
       break;
     case RDHEI_OP_EMBED:
       launch_hide(B, false, st);
@@ -261,15 +293,25 @@ int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
       launch_hide(B, true, st);
       break;
     case RDHEI_OP_DECRYPT_RECOVER:
-      launch_pass1(B, 1, p->general, st);
-      launch_topmap(B, false, st);
-      launch_dec_pass2(B, p->any_lmr, st);
+      if (stage == 0) launch_pass1(B, 1, p->general, st);
+      else if (stage == 1) launch_topmap(B, false, st);
+      else launch_dec_pass2(B, p->any_lmr, st);
       break;
     case RDHEI_OP_LMR_SET_SIDE:
       launch_lmr_side(B, st);
       break;
   }
   return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
+}
+
+int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
+  const int n = rdhei_plan_stage_count(op);
+  if (n == 0) return RDHEI_EINVAL;
+  for (int s = 0; s < n; s++) {
+    int rc = rdhei_plan_run_stage(p, op, s, stream);
+    if (rc) return rc;
+  }
+  return RDHEI_OK;
 }
 
 void rdhei_plan_destroy(rdhei_plan* p) { delete p; }

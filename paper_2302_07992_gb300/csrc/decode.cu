@@ -152,9 +152,11 @@ __global__ void __launch_bounds__(256) k_dec_pass2(Batch B) {
       if (ptx == 0) B.tile_rows[(size_t)g * 128 + 64 + row] = (uint8_t)((ch << 7) | cf);
     }
   }
-  __threadfence();
   __syncthreads();
-  if (t == 0) st_release_u32(B.tile_flags + g, ptx == 0 ? FLAG_INC : FLAG_AGG);
+  if (t == 0) {
+    __threadfence();
+    st_release_u32(B.tile_flags + g, ptx == 0 ? FLAG_INC : FLAG_AGG);
+  }
 
   // 4. look-back for the carries entering this tile from the left
   if (ptx > 0) {
@@ -168,6 +170,7 @@ __global__ void __launch_bounds__(256) k_dec_pass2(Batch B) {
         uint32_t f = ld_acquire_u32(B.tile_flags + cur);
         if (f == 0) {
           if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) { timed_out = true; break; }
+          __nanosleep(32);
           continue;
         }
         const uint8_t* rv = B.tile_rows + (size_t)cur * 128 + (f == FLAG_INC ? 64 : 0);
@@ -191,9 +194,11 @@ __global__ void __launch_bounds__(256) k_dec_pass2(Batch B) {
       const uint32_t inc = (agg >> 7) ? agg : (0x80u | rowcarry[row]);
       B.tile_rows[(size_t)g * 128 + 64 + row] = (uint8_t)inc;
     }
-    __threadfence();
     __syncthreads();
-    if (t == 0) st_release_u32(B.tile_flags + g, FLAG_INC);
+    if (t == 0) {
+      __threadfence();
+      st_release_u32(B.tile_flags + g, FLAG_INC);
+    }
     if (!in_has) { in_has = 1; in_fld = rowcarry[row]; }
   }
 

@@ -116,57 +116,70 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_hide(Batch B) {
     __syncthreads();
   }
 
-  // ---- publish the aggregate, look back for the offset -------------------------------
-  if (t == 0) {
+  // ---- publish the aggregate, look back for the offset (warp 0, 32 chunks a step) ----
+  if (warp == 0) {
     uint32_t tail = 0;
     if (EXTRACT && T > 0) tail = T >= 32 ? get_bits(lbuf, T - 32, 32) : get_bits(lbuf, 0, T);
     unsigned long long* st = B.chunk_status + g;
+    uint32_t G = 0, acc = 0;
     if (c == 0) {
-      st_release_u64(st, pack_status(2, T, tail));
-      s_G = 0; s_carry = 0;
+      if (lane == 0) st_release_u64(st, pack_status(2, T, tail));
     } else {
-      st_release_u64(st, pack_status(1, T, tail));
-      uint32_t G = 0, acc = 0, have = 0;
-      uint32_t cur = g - 1;
+      if (lane == 0) st_release_u64(st, pack_status(1, T, tail));
+      uint32_t have = 0;
+      int64_t cur = (int64_t)g - 1;                  // predecessor seen by lane 0
+      const int64_t first = (int64_t)d.chunk_base;   // the image's chunk 0 is always inclusive
       const uint64_t t0 = globaltimer_ns();
       while (true) {
-        const unsigned long long s = ld_acquire_u64(B.chunk_status + cur);
-        const uint32_t f = (uint32_t)(s >> 62);
-        if (f == 0) {
-          if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-            set_error(B.err, ERR_TIMEOUT);
-            info->status = ERR_TIMEOUT;
-            break;
+        const int64_t idx = cur - lane;
+        unsigned long long sw = 0;
+        bool late = false;
+        if (idx >= first) {
+          while (true) {
+            sw = ld_acquire_u64(B.chunk_status + idx);
+            if ((sw >> 62) != 0) break;
+            if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) { late = true; break; }
+            __nanosleep(32);
           }
-          __nanosleep(20);
-          continue;
         }
-        const uint32_t v = (uint32_t)(s >> 32) & 0x3FFFFFFFu, tl = (uint32_t)s;
-        if (f == 2) {
-          G += v;
-          if (have < 32) acc |= have == 0 ? tl : (tl << have);
-          have = 32;
+        if (__any_sync(0xffffffffu, late)) {
+          if (lane == 0) { set_error(B.err, ERR_TIMEOUT); info->status = ERR_TIMEOUT; }
           break;
         }
-        G += v;
-        if (have < 32 && v > 0) {
-          const uint32_t nb = v < 32 ? v : 32;
-          const uint32_t part = nb == 32 ? tl : (tl & ((1u << nb) - 1u));
-          acc |= have == 0 ? part : (part << have);
-          have += v;
-          if (have > 32) have = 32;
+        const uint32_t f = idx >= first ? (uint32_t)(sw >> 62) : 2u;
+        const uint32_t incm = __ballot_sync(0xffffffffu, f == 2);
+        const int L = incm ? __ffs(incm) - 1 : 31;     // lanes 0..L lie after the nearest inclusive one
+        const uint32_t v = lane <= L ? ((uint32_t)(sw >> 32) & 0x3FFFFFFFu) : 0u;
+        const uint32_t tl = (uint32_t)sw;
+        uint32_t sum = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        G += sum;
+        // the last 32 raw bits before this chunk: nearest predecessors first
+        for (int j = 0; j <= L && have < 32; j++) {
+          const uint32_t vj = __shfl_sync(0xffffffffu, v, j), tj = __shfl_sync(0xffffffffu, tl, j);
+          const uint32_t fj = __shfl_sync(0xffffffffu, f, j);
+          if (fj == 2) {
+            acc |= have == 0 ? tj : (tj << have);
+            have = 32;
+          } else if (vj) {
+            const uint32_t nb = vj < 32 ? vj : 32;
+            const uint32_t part = nb == 32 ? tj : (tj & ((1u << nb) - 1u));
+            acc |= have == 0 ? part : (part << have);
+            have = have + vj > 32 ? 32 : have + vj;
+          }
         }
-        --cur;
+        if (incm) break;
+        cur -= 32;
       }
       uint32_t itail = acc;                          // last 32 raw bits before G + T
       if (EXTRACT) {
         if (T >= 32) itail = tail;
         else if (T > 0) itail = (acc << T) | tail;
       }
-      st_release_u64(st, pack_status(2, G + T, itail));
-      s_G = G; s_carry = acc;
+      if (lane == 0) st_release_u64(st, pack_status(2, G + T, itail));
     }
-    s_T = T;
+    if (lane == 0) { s_G = G; s_carry = acc; s_T = T; }
   }
   __syncthreads();
   const uint64_t G = s_G;
@@ -202,9 +215,8 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_hide(Batch B) {
   const uint64_t blk0 = any ? (w_lo >> 4) : 0;
   const uint32_t nblk = any ? (uint32_t)((w_hi >> 4) - blk0 + 1) : 0u;
   // spread the ChaCha blocks over the warps
-  for (uint32_t j = 0; j < nblk; j++) {
-    const uint32_t owner = (j % 8) * 32 + (j / 8) % 32;
-    if ((uint32_t)t == owner) {
+  for (uint32_t j = t; j < nblk; j += HIDE_THREADS) {
+    {                        // consecutive lanes: few, full warps
       uint32_t o[16];
       chacha20_block(d.k2, (uint32_t)(blk0 + j), d.n2, o);
 #pragma unroll

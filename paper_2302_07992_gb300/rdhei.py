@@ -61,6 +61,12 @@ _lib.rdhei_plan_upload.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_si
 _lib.rdhei_plan_upload.restype = ctypes.c_int
 _lib.rdhei_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
 _lib.rdhei_plan_run.restype = ctypes.c_int
+_lib.rdhei_plan_run_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+_lib.rdhei_plan_run_stage.restype = ctypes.c_int
+_lib.rdhei_plan_stage_count.argtypes = [ctypes.c_int]
+_lib.rdhei_plan_stage_count.restype = ctypes.c_int
+_lib.rdhei_stage_name.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.rdhei_stage_name.restype = ctypes.c_char_p
 _lib.rdhei_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.rdhei_plan_destroy.restype = None
 _lib.rdhei_workspace_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
@@ -84,6 +90,11 @@ def _check(rc: int, what: str):
 
 def version() -> str:
     return _lib.rdhei_version().decode()
+
+
+def stages(op: int) -> list[str]:
+    """Names of the kernels one operation launches, in launch order."""
+    return [_lib.rdhei_stage_name(op, s).decode() for s in range(_lib.rdhei_plan_stage_count(op))]
 
 
 def library_path() -> str:
@@ -180,6 +191,10 @@ class Plan:
 
     def run(self, op: int, stream=None):
         _check(_lib.rdhei_plan_run(self._h, int(op), _stream(stream)), f"rdhei_plan_run({op})")
+
+    def run_stage(self, op: int, stage: int, stream=None):
+        _check(_lib.rdhei_plan_run_stage(self._h, int(op), int(stage), _stream(stream)),
+               f"rdhei_plan_run_stage({op}, {stage})")
 
     def status(self, stream=None) -> int:
         code = ctypes.c_int32(0)
