@@ -375,14 +375,16 @@ def roofline(res, peaks, args):
     hbm_bytes = {
         "pass1_keystream_hist": 1.0 * px,              # read I
         "enc_gather": 2.0 * px,                        # read I (gathered), write I_e
-        "embed_scan": (2.0 + der / 8) * px,            # read I_e + payload, write I_e'
-        "extract_scan": (1.0 + der / 8) * px,          # read I_e', write payload bits
+        "z2_encrypt": 2 * der / 8 * px,                # read message, write K2-encrypted message
+        "embed_scan": (2.0 + der / 8) * px,            # read I_e + encrypted message, write I_e'
+        "extract_scan": (1.0 + der / 8) * px,          # read I_e', write raw slot bits
+        "z2_decrypt": 2 * der / 8 * px,                # read + write the extracted bits
         "pass1_keystream_decrypt": 1.0 * px,           # read I_e'
         "dec_gather_recover": 1.0 * px,                # write I'
         "topmap": 0.0,
     }
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
-                "embed_scan": der / 8 * px, "extract_scan": der / 8 * px}
+                "z2_encrypt": der / 8 * px, "z2_decrypt": der / 8 * px}
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SMS * ALU_LANES_PER_SM * clock_mhz * 1e6           # ALU-pipe ops/s
     hbm_peak = peaks.get("hbm_gbs", 6777.0)
@@ -471,7 +473,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator standing in for BOWS-2)",
             "config": config, "e2e": res["e2e"], "roofline": roof, "cpu_baseline": cpu_base,
-            "clocks": res["clocks"], "gpu_launches": 8 * K,
+            "clocks": res["clocks"], "gpu_launches": len(res["stage_list"]) * K,
             "hbm_roofline_mpx": peaks.get("hbm_gbs", 6777.0) * 1e3 / (4.0 + 2 * res["verify"]["mean_der_bpp"] / 8),
             "verify": res["verify"],
             "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()}}

@@ -13,7 +13,8 @@ void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st);
 void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
 void launch_enc_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
-void launch_hide(const Batch& B, bool extract, cudaStream_t st);
+void launch_scan(const Batch& B, bool extract, cudaStream_t st);
+void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st);
 void launch_lmr_side(const Batch& B, cudaStream_t st);
 }  // namespace rdhei
 
@@ -22,12 +23,12 @@ using namespace rdhei;
 struct rdhei_plan {
   std::vector<rdhei_job> jobs;
   std::vector<ImgDesc> desc;
-  std::vector<uint32_t> tile_prefix, chunk_prefix;
-  std::vector<size_t> stash_off;
+  std::vector<uint32_t> tile_prefix, chunk_prefix, z2_prefix;
+  std::vector<size_t> stash_off, ebuf_off;
   size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
-         off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_tile_rows = 0,
+         off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_tile_rows = 0,
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, total = 0;
-  uint32_t total_tiles = 0, total_chunks = 0;
+  uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0;
   bool any_lmr = false, general = false;
   void* ws = nullptr;
   Batch batch{};
@@ -73,6 +74,8 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_chunk_prefix = off;
   off = align_up(off + (size_t)(n + 1) * 4, 256);
+  p->off_z2_prefix = off;
+  off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_tile_rows = off;
   off = align_up(off + (size_t)p->total_tiles * 128, 256);
   p->off_subtree = off;
@@ -84,9 +87,12 @@ static void build_layout(rdhei_plan* p) {
   p->off_tilemap = off;
   off = align_up(off + (size_t)p->total_tiles * sizeof(TileMap), 256);
   p->stash_off.resize(n);
+  p->ebuf_off.resize(n);
   for (int i = 0; i < n; i++) {
     p->stash_off[i] = off;
     off = align_up(off + (size_t)p->jobs[i].H * p->jobs[i].W, 256);
+    p->ebuf_off[i] = off;
+    off = align_up(off + (size_t)((p->jobs[i].nbits + 31) / 32) * 4, 256);
   }
   p->total = off;
 }
@@ -102,7 +108,8 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
   p->desc.resize(n);
   p->tile_prefix.resize(n + 1);
   p->chunk_prefix.resize(n + 1);
-  uint64_t tiles = 0, chunks = 0;
+  p->z2_prefix.resize(n + 1);
+  uint64_t tiles = 0, chunks = 0, z2 = 0;
   for (int i = 0; i < n; i++) {
     const rdhei_job& j = p->jobs[i];
     int rc = validate_job(j);
@@ -121,8 +128,12 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     d.chunk_base = (uint32_t)chunks;
     p->tile_prefix[i] = (uint32_t)tiles;
     p->chunk_prefix[i] = (uint32_t)chunks;
+    p->z2_prefix[i] = (uint32_t)z2;
     tiles += (uint64_t)d.tiles_x * d.tiles_y;
     chunks += d.nchunks;
+    // K2 keystream blocks (512 message bits each) for the hider's or receiver's message
+    const uint64_t mbits = j.nbits > d.max_bits ? j.nbits : d.max_bits;
+    z2 += (mbits + 511) / 512;
     for (int k = 0; k < 8; k++) {
       d.k1[k] = (uint32_t)j.k1[4 * k] | ((uint32_t)j.k1[4 * k + 1] << 8) | ((uint32_t)j.k1[4 * k + 2] << 16) |
                 ((uint32_t)j.k1[4 * k + 3] << 24);
@@ -138,14 +149,18 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     d.src = j.src; d.dst = j.dst; d.map_bits = j.map_bits; d.eta_bits = j.eta_bits;
     d.side_bits = j.side_bits; d.side_nbits = j.side_nbits;
     d.payload = j.payload; d.nbits = j.nbits;
-    d.bits_out = j.bits_out; d.max_bits = j.max_bits;
+    d.bits_out = j.bits_out;
+    // no image holds more than 7 bits per pixel: larger requests are capped there
+    d.max_bits = j.max_bits < 7ull * j.H * j.W ? j.max_bits : 7ull * j.H * j.W;
     d.info = j.info;
     if (j.variant == RDHEI_LMR) p->any_lmr = true;
     if (j.W % 64) p->general = true;
   }
-  if (tiles >= (1ull << 32) || chunks >= (1ull << 32)) { delete p; return RDHEI_EINVAL; }
+  if (tiles >= (1ull << 32) || chunks >= (1ull << 32) || z2 >= (1ull << 32)) { delete p; return RDHEI_EINVAL; }
   p->tile_prefix[n] = (uint32_t)tiles;
   p->chunk_prefix[n] = (uint32_t)chunks;
+  p->z2_prefix[n] = (uint32_t)z2;
+  p->total_z2 = (uint32_t)z2;
   p->total_tiles = (uint32_t)tiles;
   p->total_chunks = (uint32_t)chunks;
   build_layout(p);
@@ -162,13 +177,17 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* base = reinterpret_cast<uint8_t*>(ws);
   const int n = (int)p->jobs.size();
-  for (int i = 0; i < n; i++) p->desc[i].stash = base + p->stash_off[i];
+  for (int i = 0; i < n; i++) {
+    p->desc[i].stash = base + p->stash_off[i];
+    p->desc[i].ebuf = base + p->ebuf_off[i];
+  }
   // one host image of the descriptor region, copied once
-  const size_t lo = p->off_desc, hi = p->off_chunk_prefix + (size_t)(n + 1) * 4;
+  const size_t lo = p->off_desc, hi = p->off_z2_prefix + (size_t)(n + 1) * 4;
   std::vector<uint8_t> host(hi - lo, 0);
   if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
   std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host.data() + (p->off_z2_prefix - lo), p->z2_prefix.data(), (size_t)(n + 1) * 4);
   if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return RDHEI_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
@@ -177,6 +196,8 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.desc = reinterpret_cast<const ImgDesc*>(base + p->off_desc);
   B.tile_prefix = reinterpret_cast<const uint32_t*>(base + p->off_tile_prefix);
   B.chunk_prefix = reinterpret_cast<const uint32_t*>(base + p->off_chunk_prefix);
+  B.z2_prefix = reinterpret_cast<const uint32_t*>(base + p->off_z2_prefix);
+  B.total_z2_blocks = p->total_z2;
   B.n_images = n;
   B.total_tiles = p->total_tiles;
   B.total_chunks = p->total_chunks;
@@ -238,6 +259,7 @@ int rdhei_plan_stage_count(int op) {
       return 3;
     case RDHEI_OP_EMBED:
     case RDHEI_OP_EXTRACT:
+      return 2;
     case RDHEI_OP_LMR_SET_SIDE:
       return 1;
     default:
@@ -251,8 +273,8 @@ const char* rdhei_stage_name(int op, int stage) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
     case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 3 ? dec[stage] : "";
-    case RDHEI_OP_EMBED: return stage == 0 ? "embed_scan" : "";
-    case RDHEI_OP_EXTRACT: return stage == 0 ? "extract_scan" : "";
+    case RDHEI_OP_EMBED: return stage == 0 ? "z2_encrypt" : stage == 1 ? "embed_scan" : "";
+    case RDHEI_OP_EXTRACT: return stage == 0 ? "extract_scan" : stage == 1 ? "z2_decrypt" : "";
     case RDHEI_OP_LMR_SET_SIDE: return stage == 0 ? "lmr_side" : "";
   }
   return "";
@@ -287,10 +309,12 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       else launch_enc_pass2(B, p->any_lmr, st);
       break;
     case RDHEI_OP_EMBED:
-      launch_hide(B, false, st);
+      if (stage == 0) launch_z2_xor(B, false, st);
+      else launch_scan(B, false, st);
       break;
     case RDHEI_OP_EXTRACT:
-      launch_hide(B, true, st);
+      if (stage == 0) launch_scan(B, true, st);
+      else launch_z2_xor(B, true, st);
       break;
     case RDHEI_OP_DECRYPT_RECOVER:
       if (stage == 0) launch_pass1(B, 1, p->general, st);

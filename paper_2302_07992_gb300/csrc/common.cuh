@@ -19,7 +19,7 @@ constexpr int TILE = 64;                 // tile side (pixels)
 constexpr int TILE_PX = TILE * TILE;
 constexpr int SUBTREE_BYTES = 352;       // packed 2-bit angles of levels 1..6 (342 used)
 constexpr int AUX_BYTES = 512;           // one bit per tile pixel, tile-major
-constexpr int CHUNK_PX = 4096;           // raster chunk of the payload scans
+constexpr int CHUNK_PX = 8192;           // raster chunk of the payload scans
 constexpr int ROWVAL_BYTES = 64;         // per-tile row carries of the recovery scan
 constexpr int NO_ROTATION = 99;          // lmin value that disables every level
 
@@ -43,6 +43,7 @@ struct ImgDesc {
   uint64_t max_bits;
   void* info;                 // rdhei_info*
   uint8_t* stash;             // N_px bytes: keystream (encode) / decrypted image (decode)
+  uint8_t* ebuf;              // hider: the K2-encrypted message, ceil(nbits / 32) words
   int32_t H, W, variant, b;   // b: 0 = from info (hider / receiver) or auto (owner)
   int32_t lmin, nlev;         // effective smallest level (NO_ROTATION = none), n
   uint32_t tiles_x, tiles_y, tile_base, chunk_base, nchunks;
@@ -63,6 +64,8 @@ struct Batch {
   const ImgDesc* desc;
   const uint32_t* tile_prefix;    // n + 1 entries: first global tile of each image
   const uint32_t* chunk_prefix;   // n + 1 entries
+  const uint32_t* z2_prefix;      // n + 1 entries: first K2 keystream block of each image
+  uint32_t total_z2_blocks;
   int n_images;
   uint32_t total_tiles, total_chunks;
   uint32_t* err;                  // workspace error word
