@@ -132,7 +132,8 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     tiles += (uint64_t)d.tiles_x * d.tiles_y;
     chunks += d.nchunks;
     // K2 keystream blocks (512 message bits each) for the hider's or receiver's message
-    const uint64_t mbits = j.nbits > d.max_bits ? j.nbits : d.max_bits;
+    const uint64_t capped = j.max_bits < 7ull * j.H * j.W ? j.max_bits : 7ull * j.H * j.W;
+    const uint64_t mbits = j.nbits > capped ? j.nbits : capped;
     z2 += (mbits + 511) / 512;
     for (int k = 0; k < 8; k++) {
       d.k1[k] = (uint32_t)j.k1[4 * k] | ((uint32_t)j.k1[4 * k + 1] << 8) | ((uint32_t)j.k1[4 * k + 2] << 16) |
