@@ -376,7 +376,9 @@ def roofline(res, peaks, args):
         "pass1_keystream_hist": 1.0 * px,              # read I
         "enc_gather": 2.0 * px,                        # read I (gathered), write I_e
         "z2_encrypt": 2 * der / 8 * px,                # read message, write K2-encrypted message
+        "embed_count": 0.5 * px,                       # read the map (EMR: LSB plane; LMR: packed map)
         "embed_scan": (2.0 + der / 8) * px,            # read I_e + encrypted message, write I_e'
+        "extract_count": 0.5 * px,
         "extract_scan": (1.0 + der / 8) * px,          # read I_e', write raw slot bits
         "z2_decrypt": 2 * der / 8 * px,                # read + write the extracted bits
         "pass1_keystream_decrypt": 1.0 * px,           # read I_e'

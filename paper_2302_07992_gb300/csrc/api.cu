@@ -13,6 +13,7 @@ void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st);
 void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
 void launch_enc_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
+void launch_count(const Batch& B, bool extract, cudaStream_t st);
 void launch_scan(const Batch& B, bool extract, cudaStream_t st);
 void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st);
 void launch_lmr_side(const Batch& B, cudaStream_t st);
@@ -23,12 +24,12 @@ using namespace rdhei;
 struct rdhei_plan {
   std::vector<rdhei_job> jobs;
   std::vector<ImgDesc> desc;
-  std::vector<uint32_t> tile_prefix, chunk_prefix, z2_prefix;
+  std::vector<uint32_t> tile_prefix, chunk_prefix, z2_prefix, strip_prefix;
   std::vector<size_t> stash_off, ebuf_off;
   size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
-         off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_tile_rows = 0,
+         off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_strip_prefix = 0, off_tile_rows = 0,
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, total = 0;
-  uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0;
+  uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0;
   bool any_lmr = false, general = false;
   void* ws = nullptr;
   Batch batch{};
@@ -76,6 +77,8 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_z2_prefix = off;
   off = align_up(off + (size_t)(n + 1) * 4, 256);
+  p->off_strip_prefix = off;
+  off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_tile_rows = off;
   off = align_up(off + (size_t)p->total_tiles * 128, 256);
   p->off_subtree = off;
@@ -109,7 +112,8 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
   p->tile_prefix.resize(n + 1);
   p->chunk_prefix.resize(n + 1);
   p->z2_prefix.resize(n + 1);
-  uint64_t tiles = 0, chunks = 0, z2 = 0;
+  p->strip_prefix.resize(n + 1);
+  uint64_t tiles = 0, chunks = 0, z2 = 0, strips = 0;
   for (int i = 0; i < n; i++) {
     const rdhei_job& j = p->jobs[i];
     int rc = validate_job(j);
@@ -129,6 +133,8 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     p->tile_prefix[i] = (uint32_t)tiles;
     p->chunk_prefix[i] = (uint32_t)chunks;
     p->z2_prefix[i] = (uint32_t)z2;
+    p->strip_prefix[i] = (uint32_t)strips;
+    strips += d.tiles_y;
     tiles += (uint64_t)d.tiles_x * d.tiles_y;
     chunks += d.nchunks;
     // K2 keystream blocks (512 message bits each) for the hider's or receiver's message
@@ -161,6 +167,8 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
   p->tile_prefix[n] = (uint32_t)tiles;
   p->chunk_prefix[n] = (uint32_t)chunks;
   p->z2_prefix[n] = (uint32_t)z2;
+  p->strip_prefix[n] = (uint32_t)strips;
+  p->total_strips = (uint32_t)strips;
   p->total_z2 = (uint32_t)z2;
   p->total_tiles = (uint32_t)tiles;
   p->total_chunks = (uint32_t)chunks;
@@ -183,12 +191,13 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
     p->desc[i].ebuf = base + p->ebuf_off[i];
   }
   // one host image of the descriptor region, copied once
-  const size_t lo = p->off_desc, hi = p->off_z2_prefix + (size_t)(n + 1) * 4;
+  const size_t lo = p->off_desc, hi = p->off_strip_prefix + (size_t)(n + 1) * 4;
   std::vector<uint8_t> host(hi - lo, 0);
   if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
   std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_z2_prefix - lo), p->z2_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host.data() + (p->off_strip_prefix - lo), p->strip_prefix.data(), (size_t)(n + 1) * 4);
   if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return RDHEI_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
@@ -199,6 +208,8 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.chunk_prefix = reinterpret_cast<const uint32_t*>(base + p->off_chunk_prefix);
   B.z2_prefix = reinterpret_cast<const uint32_t*>(base + p->off_z2_prefix);
   B.total_z2_blocks = p->total_z2;
+  B.strip_prefix = reinterpret_cast<const uint32_t*>(base + p->off_strip_prefix);
+  B.total_strips = p->total_strips;
   B.n_images = n;
   B.total_tiles = p->total_tiles;
   B.total_chunks = p->total_chunks;
@@ -257,10 +268,9 @@ int rdhei_plan_stage_count(int op) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT:
     case RDHEI_OP_DECRYPT_RECOVER:
-      return 3;
     case RDHEI_OP_EMBED:
     case RDHEI_OP_EXTRACT:
-      return 2;
+      return 3;
     case RDHEI_OP_LMR_SET_SIDE:
       return 1;
     default:
@@ -274,8 +284,9 @@ const char* rdhei_stage_name(int op, int stage) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
     case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 3 ? dec[stage] : "";
-    case RDHEI_OP_EMBED: return stage == 0 ? "z2_encrypt" : stage == 1 ? "embed_scan" : "";
-    case RDHEI_OP_EXTRACT: return stage == 0 ? "extract_scan" : stage == 1 ? "z2_decrypt" : "";
+    case RDHEI_OP_EMBED: return stage == 0 ? "z2_encrypt" : stage == 1 ? "embed_count" : stage == 2 ? "embed_scan" : "";
+    case RDHEI_OP_EXTRACT:
+      return stage == 0 ? "extract_count" : stage == 1 ? "extract_scan" : stage == 2 ? "z2_decrypt" : "";
     case RDHEI_OP_LMR_SET_SIDE: return stage == 0 ? "lmr_side" : "";
   }
   return "";
@@ -311,10 +322,12 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       break;
     case RDHEI_OP_EMBED:
       if (stage == 0) launch_z2_xor(B, false, st);
+      else if (stage == 1) launch_count(B, false, st);
       else launch_scan(B, false, st);
       break;
     case RDHEI_OP_EXTRACT:
-      if (stage == 0) launch_scan(B, true, st);
+      if (stage == 0) launch_count(B, true, st);
+      else if (stage == 1) launch_scan(B, true, st);
       else launch_z2_xor(B, true, st);
       break;
     case RDHEI_OP_DECRYPT_RECOVER:

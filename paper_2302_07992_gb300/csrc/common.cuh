@@ -65,6 +65,8 @@ struct Batch {
   const uint32_t* tile_prefix;    // n + 1 entries: first global tile of each image
   const uint32_t* chunk_prefix;   // n + 1 entries
   const uint32_t* z2_prefix;      // n + 1 entries: first K2 keystream block of each image
+  const uint32_t* strip_prefix;   // n + 1 entries: first 64-row strip of each image
+  uint32_t total_strips;
   uint32_t total_z2_blocks;
   int n_images;
   uint32_t total_tiles, total_chunks;

@@ -2,21 +2,19 @@
 // Sec. III-B-3; Eq. roration2): de-rotate the decrypted image held in the stash and
 // restore the replaced MSBs from the last label-1 pixel to the left.
 //
-// The restoration only looks left along a row (omega glide), so tile (r, c) depends
-// on tile (r, c - 1) only.  Tiles are taken in ticket order (row-major per image) and
-// hand the per-row carry ("field of the last label-1 pixel so far") to their right
-// neighbour with a decoupled look-back: each tile publishes its own row aggregates
-// at once and its inclusive carries once its left neighbour's are known.
+// The restoration only looks left along a row (omega glide), so the tiles of a
+// 64-row strip depend on each other from left to right and strips are independent.
+// One CTA walks one strip: per tile it gathers the rotated tile (micro-block
+// de-rotation, permute.cuh), restores the fields inside the tile, and carries, per
+// row, the field of the last label-1 pixel into the next tile.  The next tile's
+// data is fetched into registers while the current one is processed.
 #include "permute.cuh"
 #include "../../include/rdhei.h"
 
 namespace rdhei {
 
-constexpr uint32_t FLAG_AGG = 1, FLAG_INC = 2;
-constexpr int TK_DEC = 0;
-
 template <bool ANY_LMR>
-__global__ void __launch_bounds__(256) k_dec_pass2(Batch B) {
+__global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t ain[TILE * TPITCH];
   __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
@@ -24,211 +22,162 @@ __global__ void __launch_bounds__(256) k_dec_pass2(Batch B) {
   __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
   __shared__ uint32_t selt[16];
   __shared__ uint8_t rowcarry[TILE];
-  __shared__ uint32_t s_ticket;
 
   const int t = threadIdx.x;
-  if (t == 0) s_ticket = atomicAdd(B.tickets + TK_DEC, 1u);
-  __syncthreads();
-  const uint32_t g = s_ticket;
-  const int img = owner_of(B.tile_prefix, B.n_images, g);
+  const uint32_t s = blockIdx.x;
+  const int img = owner_of(B.strip_prefix, B.n_images, s);
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W;
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
   const int b = d.b > 0 ? d.b : info->b;
   const bool lmr = ANY_LMR && d.variant == RDHEI_LMR;
-  const uint32_t P = g - d.tile_base;
-  const int ptx = (int)(P % d.tiles_x);
-  const int py0 = (int)(P / d.tiles_x) * TILE, px0 = ptx * TILE;
-  const TileMap tm = B.tilemap[g];
-  const uint32_t Q = tm.dec_dst, U = tm.dec_shi;
-  const int qy0 = (int)(Q / d.tiles_x) * TILE, qx0 = (int)(Q % d.tiles_x) * TILE;
+  const uint32_t ty = s - __ldg(B.strip_prefix + img);
+  const uint32_t tiles_x = d.tiles_x;
   // the replaced field: EMR top b bits, LMR bits 6 .. 8-b (Sec. III-B-2)
   const uint32_t FM = lmr ? (((1u << (b - 1)) - 1u) << (8 - b)) : ((0xFFu << (8 - b)) & 0xFFu);
-
-  {
-    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(B.subtree + (size_t)(d.tile_base + P) * SUBTREE_BYTES);
-    if (t < SUBTREE_BYTES / 4) reinterpret_cast<uint32_t*>(sub)[t] = __ldg(s32 + t);
-    // inverse turns of the 2x2 sub-blocks
-    if (t < 16) selt[t] = pair_selectors((4u - (t & 3u)) & 3u, (4u - (t >> 2)) & 3u);
-  }
-
+  const uint32_t FM4 = FM * 0x01010101u;
   const int row = t >> 2, quarter = t & 3;
-  // 1. load the decrypted tile Q from the stash, and its aux plane
-  {
-    const int y = qy0 + row, x = qx0 + 16 * quarter;
-    int valid = (y < H) ? min(16, W - x) : 0;
+  const int y = (int)ty * TILE + row;
+  if (t < 16) selt[t] = pair_selectors((4u - (t & 3u)) & 3u, (4u - (t >> 2)) & 3u);   // inverse 2x2 turns
+
+  // rotated tile of original tile (ty, tx): my 16 bytes of the stash and 16 aux bits
+  uint32_t nw[4], na = 0, nU = 0;
+  auto fetch = [&](uint32_t tx) {
+    const uint32_t g = d.tile_base + ty * tiles_x + tx;
+    const TileMap tm = B.tilemap[g];
+    nU = tm.dec_shi;
+    const uint32_t Q = tm.dec_dst;
+    const int qy = (int)(Q / tiles_x) * TILE + row, qx = (int)(Q % tiles_x) * TILE + 16 * quarter;
+    int valid = (qy < H) ? min(16, W - qx) : 0;
     if (valid < 0) valid = 0;
-    const uint8_t* s = d.stash + (size_t)y * W + x;
-    uint32_t w[4];
-    if (valid == 16 && ((reinterpret_cast<uintptr_t>(s) & 15) == 0)) {
-      uint4 v = *reinterpret_cast<const uint4*>(s);
-      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    const uint8_t* sp = d.stash + (size_t)qy * W + qx;
+    if (valid == 16 && ((reinterpret_cast<uintptr_t>(sp) & 15) == 0)) {
+      const uint4 v = *reinterpret_cast<const uint4*>(sp);
+      nw[0] = v.x; nw[1] = v.y; nw[2] = v.z; nw[3] = v.w;
     } else {
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         uint32_t v = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-          if (4 * i + k < valid) v |= (uint32_t)s[4 * i + k] << (8 * k);
-        w[i] = v;
+          if (4 * i + k < valid) v |= (uint32_t)sp[4 * i + k] << (8 * k);
+        nw[i] = v;
       }
     }
-    *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) = make_uint4(w[0], w[1], w[2], w[3]);
-    const uint64_t arow = reinterpret_cast<const uint64_t*>(B.aux + (size_t)(d.tile_base + Q) * AUX_BYTES)[row];
-    const uint32_t a16 = (uint32_t)(arow >> (16 * quarter)) & 0xFFFFu;
-    uint32_t e[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) e[i] = (((a16 >> (4 * i)) & 0xFu) * 0x00204081u) & 0x01010101u;
-    *reinterpret_cast<uint4*>(ain + row * TPITCH + 16 * quarter) = make_uint4(e[0], e[1], e[2], e[3]);
-  }
-  __syncthreads();
+    const uint16_t* ap = reinterpret_cast<const uint16_t*>(B.aux + (size_t)(d.tile_base + Q) * AUX_BYTES);
+    na = ap[row * 4 + quarter];
+  };
+  fetch(0);
 
-  // 2. de-rotation: original micro-block (mr, mc) <- rotated micro-block (qr, qc)
-  {
-    const uint32_t mr = t >> 4, mc = t & 15;
-    uint32_t qr, qc, S1;
-    dec_microblock_src(sub, U, mr, mc, qr, qc, S1);
-    const uint32_t nib = sub_level1_nibbles(sub, mr, mc);
-    const uint32_t sT = selt[nib & 0xF], sB = selt[nib >> 4];
-    const uint32_t inv = (4u - S1) & 3u;
-    uint32_t w0, w1, w2, w3;
-    ld_micro(tin, qr, qc, w0, w1, w2, w3);
-    turn4x4(w0, w1, w2, w3, inv);
-    turn_subblocks(w0, w1, w2, w3, sT, sB);
-    st_micro(tout, mr, mc, w0, w1, w2, w3);
-    ld_micro(ain, qr, qc, w0, w1, w2, w3);
-    turn4x4(w0, w1, w2, w3, inv);
-    turn_subblocks(w0, w1, w2, w3, sT, sB);
-    st_micro(aout, mr, mc, w0, w1, w2, w3);
-  }
-  __syncthreads();
-
-  // 3. labels and decrypted values in the original frame
-  const int y = py0 + row, x = px0 + 16 * quarter;
-  int valid = (y < H) ? min(16, W - x) : 0;
-  if (valid < 0) valid = 0;
-  uint32_t v[4], lab[4];
-  {
-    const uint4 v4 = *reinterpret_cast<const uint4*>(tout + row * TPITCH + 16 * quarter);
-    const uint4 a4 = *reinterpret_cast<const uint4*>(aout + row * TPITCH + 16 * quarter);
-    const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w}, aa[4] = {a4.x, a4.y, a4.z, a4.w};
+  for (uint32_t tx = 0; tx < tiles_x; tx++) {
+    const uint32_t P = ty * tiles_x + tx;
+    const uint32_t U = nU;
+    // 1. the fetched tile and its aux plane into shared memory, the subtree of P
+    *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    {
+      uint32_t e[4];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      if (lmr) {
-        lab[i] = (vv[i] >> 7) & 0x01010101u;
-        v[i] = (vv[i] & 0x7F7F7F7Fu) | (aa[i] << 7);            // bit 7 := eta
-      } else {
-        lab[i] = vv[i] & 0x01010101u;
-        v[i] = vv[i] ^ aa[i];                                   // LSB := map XOR s (decrypted LSB)
-      }
-      // pixels past the row end are never label 1
-      int nv = valid - 4 * i;
-      lab[i] &= nv <= 0 ? 0u : nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+      for (int i = 0; i < 4; i++) e[i] = (((na >> (4 * i)) & 0xFu) * 0x00204081u) & 0x01010101u;
+      *reinterpret_cast<uint4*>(ain + row * TPITCH + 16 * quarter) = make_uint4(e[0], e[1], e[2], e[3]);
     }
-    if (x == 0 && valid > 0) lab[0] |= 1u;                      // first image column: non-redundant
-  }
-  // segment aggregate: field of the last label-1 pixel among my 16
-  uint32_t has = 0, fld = 0;
+    if (t < SUBTREE_BYTES / 4)
+      reinterpret_cast<uint32_t*>(sub)[t] =
+          __ldg(reinterpret_cast<const uint32_t*>(B.subtree + (size_t)(d.tile_base + P) * SUBTREE_BYTES) + t);
+    if (tx + 1 < tiles_x) fetch(tx + 1);        // in flight while this tile is processed
+    __syncthreads();
+
+    // 2. de-rotation: original micro-block (mr, mc) <- rotated micro-block (qr, qc)
+    {
+      const uint32_t mr = t >> 4, mc = t & 15;
+      uint32_t qr, qc, S1;
+      dec_microblock_src(sub, U, mr, mc, qr, qc, S1);
+      const uint32_t nib = sub_level1_nibbles(sub, mr, mc);
+      const uint32_t sT = selt[nib & 0xF], sB = selt[nib >> 4];
+      const uint32_t inv = (4u - S1) & 3u;
+      uint32_t w0, w1, w2, w3;
+      ld_micro(tin, qr, qc, w0, w1, w2, w3);
+      turn4x4(w0, w1, w2, w3, inv);
+      turn_subblocks(w0, w1, w2, w3, sT, sB);
+      st_micro(tout, mr, mc, w0, w1, w2, w3);
+      ld_micro(ain, qr, qc, w0, w1, w2, w3);
+      turn4x4(w0, w1, w2, w3, inv);
+      turn_subblocks(w0, w1, w2, w3, sT, sB);
+      st_micro(aout, mr, mc, w0, w1, w2, w3);
+    }
+    __syncthreads();
+
+    // 3. labels and decrypted values; inside my 16 pixels every label-0 pixel takes the
+    //    field of the last label-1 pixel to its left (log-step over the bytes of a word,
+    //    then word to word)
+    const int x = (int)tx * TILE + 16 * quarter;
+    int valid = (y < H) ? min(16, W - x) : 0;
+    if (valid < 0) valid = 0;
+    uint32_t v[4], xf[4], mm[4];
+    {
+      const uint4 v4 = *reinterpret_cast<const uint4*>(tout + row * TPITCH + 16 * quarter);
+      const uint4 a4 = *reinterpret_cast<const uint4*>(aout + row * TPITCH + 16 * quarter);
+      const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w}, aa[4] = {a4.x, a4.y, a4.z, a4.w};
+      uint32_t carry = 0, carried = 0;
 #pragma unroll
-  for (int i = 0; i < 16; i++) {
-    const uint32_t li = (lab[i >> 2] >> (8 * (i & 3))) & 1u;
-    const uint32_t fi = ((v[i >> 2] >> (8 * (i & 3))) & FM) >> (8 - b);
-    if (li) { has = 1; fld = fi; }
-  }
-  // exclusive combine across the 4 quarters of the row (lanes 4k..4k+3)
-  uint32_t in_has = 0, in_fld = 0;
-  {
-    uint32_t ch = has, cf = fld;   // inclusive scan, "last one wins"
+      for (int i = 0; i < 4; i++) {
+        uint32_t lab;
+        if (lmr) {
+          lab = (vv[i] >> 7) & 0x01010101u;
+          v[i] = (vv[i] & 0x7F7F7F7Fu) | (aa[i] << 7);            // bit 7 := eta
+        } else {
+          lab = vv[i] & 0x01010101u;
+          v[i] = vv[i] ^ aa[i];                                   // LSB := map XOR s (decrypted LSB)
+        }
+        const int nv = valid - 4 * i;                             // pixels past the row end: label 0
+        lab &= nv <= 0 ? 0u : nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+        if (i == 0 && x == 0 && valid > 0) lab |= 1u;             // first image column: non-redundant
+        uint32_t m = lab * 0xFFu;
+        uint32_t f = v[i] & FM4 & m;
+        f |= ~m & (f << 8);  m |= m << 8;
+        f |= ~m & (f << 16); m |= m << 16;
+        f |= ~m & carry;     m |= carried;
+        xf[i] = f; mm[i] = m;
+        carry = (f >> 24) * 0x01010101u;
+        carried = (uint32_t)((int32_t)m >> 31);
+      }
+    }
+    // 4. carry into my 16 pixels: the last label-1 field of the quarters to my left,
+    //    else the strip's carry from the previous tile
+    const uint32_t has = mm[3] >> 31, fld = (xf[3] >> 24) & FM;
+    uint32_t ch = has, cf = fld;   // inclusive scan across the row's 4 lanes, "last one wins"
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {
-      uint32_t oh = __shfl_up_sync(0xffffffffu, ch, o, 4), of = __shfl_up_sync(0xffffffffu, cf, o, 4);
+      const uint32_t oh = __shfl_up_sync(0xffffffffu, ch, o, 4), of = __shfl_up_sync(0xffffffffu, cf, o, 4);
       if (quarter >= o && !ch) { ch = oh; cf = of; }
     }
-    in_has = __shfl_up_sync(0xffffffffu, ch, 1, 4);
-    in_fld = __shfl_up_sync(0xffffffffu, cf, 1, 4);
-    if (quarter == 0) { in_has = 0; in_fld = 0; }
-    if (quarter == 3) {
-      B.tile_rows[(size_t)g * 128 + row] = (uint8_t)((ch << 7) | cf);        // aggregate
-      if (ptx == 0) B.tile_rows[(size_t)g * 128 + 64 + row] = (uint8_t)((ch << 7) | cf);
-    }
-  }
-  __syncthreads();
-  if (t == 0) {
-    __threadfence();
-    st_release_u32(B.tile_flags + g, ptx == 0 ? FLAG_INC : FLAG_AGG);
-  }
+    uint32_t in_has = __shfl_up_sync(0xffffffffu, ch, 1, 4), in_fld = __shfl_up_sync(0xffffffffu, cf, 1, 4);
+    if (quarter == 0) in_has = 0;
+    if (!in_has) in_fld = tx > 0 ? rowcarry[row] : 0u;
+    __syncwarp();
+    if (quarter == 3 && ch) rowcarry[row] = (uint8_t)cf;      // carry into the next tile
 
-  // 4. look-back for the carries entering this tile from the left
-  if (ptx > 0) {
-    if (t < 32) {
-      uint32_t need = 3u;                       // rows t and t + 32 unresolved
-      uint32_t c0 = 0, c1 = 0;
-      uint32_t cur = g - 1;
-      const uint64_t t0 = globaltimer_ns();
-      bool timed_out = false;
-      while (need) {
-        uint32_t f = ld_acquire_u32(B.tile_flags + cur);
-        if (f == 0) {
-          if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) { timed_out = true; break; }
-          __nanosleep(32);
-          continue;
-        }
-        const uint8_t* rv = B.tile_rows + (size_t)cur * 128 + (f == FLAG_INC ? 64 : 0);
-        const uint32_t r0 = rv[t], r1 = rv[t + 32];
-        if ((need & 1u) && (r0 >> 7)) { c0 = r0 & 0x7Fu; need &= ~1u; }
-        if ((need & 2u) && (r1 >> 7)) { c1 = r1 & 0x7Fu; need &= ~2u; }
-        if (f == FLAG_INC) need = 0;           // an inclusive value always has a label-1 pixel
-        if (cur == d.tile_base) break;
-        --cur;
-      }
-      if (timed_out) {
-        set_error(B.err, ERR_TIMEOUT);
-        const_cast<rdhei_info*>(info)->status = ERR_TIMEOUT;
-      }
-      rowcarry[t] = (uint8_t)c0;
-      rowcarry[t + 32] = (uint8_t)c1;
-    }
-    __syncthreads();
-    if (quarter == 3) {
-      const uint32_t agg = B.tile_rows[(size_t)g * 128 + row];
-      const uint32_t inc = (agg >> 7) ? agg : (0x80u | rowcarry[row]);
-      B.tile_rows[(size_t)g * 128 + 64 + row] = (uint8_t)inc;
-    }
-    __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      st_release_u32(B.tile_flags + g, FLAG_INC);
-    }
-    if (!in_has) { in_has = 1; in_fld = rowcarry[row]; }
-  }
-
-  // 5. restore: label-0 pixels take the field of the last label-1 pixel to their left
-  if (valid > 0) {
-    uint32_t c = in_fld << (8 - b);
+    // 5. restore and store
+    if (valid > 0) {
+      const uint32_t C4 = in_fld * 0x01010101u;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      uint32_t o = v[i];
+      for (int i = 0; i < 4; i++) v[i] = (v[i] & ~FM4) | xf[i] | (~mm[i] & C4);
+      uint8_t* dst = d.dst + (size_t)y * W + x;
+      if (valid == 16 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+      } else {
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const uint32_t sh = 8 * k;
-        if ((lab[i] >> sh) & 1u) c = (o >> sh) & FM;
-        else o = (o & ~(FM << sh)) | (c << sh);
+        for (int k = 0; k < 16; k++)
+          if (k < valid) dst[k] = (uint8_t)(v[k >> 2] >> (8 * (k & 3)));
       }
-      v[i] = o;
     }
-    uint8_t* dst = d.dst + (size_t)y * W + x;
-    if (valid == 16 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-      *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
-    } else {
-      for (int k = 0; k < valid; k++) dst[k] = (uint8_t)(v[k >> 2] >> (8 * (k & 3)));
-    }
+    __syncthreads();   // shared tiles are rewritten by the next iteration
   }
 }
 
 void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st) {
-  if (B.total_tiles == 0) return;
-  if (any_lmr) k_dec_pass2<true><<<B.total_tiles, 256, 0, st>>>(B);
-  else k_dec_pass2<false><<<B.total_tiles, 256, 0, st>>>(B);
+  if (B.total_strips == 0) return;
+  if (any_lmr) k_dec_strip<true><<<B.total_strips, 256, 0, st>>>(B);
+  else k_dec_strip<false><<<B.total_strips, 256, 0, st>>>(B);
 }
 
 }  // namespace rdhei

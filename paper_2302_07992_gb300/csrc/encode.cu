@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
       if (vec) {
         *reinterpret_cast<uint4*>(dst) = make_uint4(e[0], e[1], e[2], e[3]);
       } else {
-        for (int c = 0; c < valid; c++) dst[c] = (uint8_t)(e[c >> 2] >> (8 * (c & 3)));
+#pragma unroll
+        for (int c = 0; c < 16; c++)
+          if (c < valid) dst[c] = (uint8_t)(e[c >> 2] >> (8 * (c & 3)));
       }
     }
   }

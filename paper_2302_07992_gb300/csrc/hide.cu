@@ -7,27 +7,20 @@
 //             per thread over the message), then write e into the slots (k_scan);
 //   receiver: concatenate the slots (k_scan), then decrypt with K2 (k_z2_xor).
 // A pixel's first slot index is an exclusive prefix sum of slots over the raster.
-// Chunks of 8192 pixels are taken in ticket order; each scans its own pixels
-// (warp shuffles), publishes its slot count, then finds its offset with a decoupled
-// look-back over up to 32 predecessors per step.  The status word of a chunk packs a
-// flag (2 bits), a 30-bit count or inclusive prefix, and the last 32 raw stream bits
-// up to that point, which the extractor uses to complete the 32-bit word it shares
-// with earlier chunks.
+// The scan is reduce-then-scan over chunks of 8192 pixels: k_count counts each
+// chunk's slots and the last CTA of an image turns the counts into offsets; k_scan
+// then writes (hider) or gathers (receiver) each chunk's slots at its offset.  No CTA
+// ever waits for another.
 #include "common.cuh"
 #include "../../include/rdhei.h"
 
 namespace rdhei {
 
-constexpr int TK_HIDE = 1;
 constexpr int HIDE_THREADS = 256;
 constexpr int HIDE_PX = 32;                          // pixels per thread
 constexpr int SCAN_PX = HIDE_THREADS * HIDE_PX;      // 8192 pixels per chunk
 static_assert(SCAN_PX == CHUNK_PX, "chunk size shared with the host layout");
 constexpr int SBUF_WORDS = 7 * SCAN_PX / 32 + 4;     // slots of one chunk, in 32-bit words
-
-__device__ __forceinline__ unsigned long long pack_status(uint32_t flag, uint32_t value, uint32_t tail) {
-  return ((unsigned long long)flag << 62) | ((unsigned long long)(value & 0x3FFFFFFFu) << 32) | tail;
-}
 
 // n (1..32) bits of an MSB-first word array starting at bit idx, right-aligned
 __device__ __forceinline__ uint32_t get_bits(const uint32_t* buf, uint32_t idx, uint32_t n) {
@@ -44,240 +37,351 @@ __device__ __forceinline__ void or_bits(uint32_t* buf, uint32_t idx, uint32_t va
   if (lo) atomicOr(buf + w + 1, lo);
 }
 
-// Decoupled look-back by one warp: the exclusive slot offset G of chunk g and the last
-// 32 raw stream bits before it.  Publishes the chunk's aggregate first, its inclusive
-// value after.  Image chunk 0 is inclusive at once.
-template <bool EXTRACT>
-__device__ __forceinline__ void lookback(const Batch& B, const ImgDesc& d, rdhei_info* info, uint32_t g, uint32_t c,
-                                         uint32_t T, uint32_t tail, uint32_t& G_out, uint32_t& carry_out) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long* st = B.chunk_status + g;
-  uint32_t G = 0, acc = 0;
-  if (c == 0) {
-    if (lane == 0) st_release_u64(st, pack_status(2, T, tail));
-  } else {
-    if (lane == 0) st_release_u64(st, pack_status(1, T, tail));
-    uint32_t have = 0;
-    int64_t cur = (int64_t)g - 1;
-    const int64_t first = (int64_t)d.chunk_base;
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
-      const int64_t idx = cur - lane;
-      unsigned long long sw = 0;
-      bool late = false;
-      if (idx >= first) {
-        while (true) {
-          sw = ld_acquire_u64(B.chunk_status + idx);
-          if ((sw >> 62) != 0) break;
-          if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) { late = true; break; }
-          __nanosleep(32);
-        }
-      }
-      if (__any_sync(0xffffffffu, late)) {
-        if (lane == 0) { set_error(B.err, ERR_TIMEOUT); info->status = ERR_TIMEOUT; }
-        break;
-      }
-      const uint32_t f = idx >= first ? (uint32_t)(sw >> 62) : 2u;
-      const uint32_t incm = __ballot_sync(0xffffffffu, f == 2);
-      const int L = incm ? __ffs(incm) - 1 : 31;       // lanes 0..L follow the nearest inclusive one
-      const uint32_t v = lane <= L ? ((uint32_t)(sw >> 32) & 0x3FFFFFFFu) : 0u;
-      uint32_t sum = v;
+// My 32 pixels of a chunk (raw words, loads in flight until first use) and the mask
+// of the redundant (label-0) ones: EMR reads the map from the LSB plane, LMR from the
+// packed rotated map.
+struct ChunkPx {
+  uint32_t px[8];
+  uint32_t lbits;   // LMR: packed map bits of my 32 pixels
+  int valid;
+};
+
+__device__ __forceinline__ void issue_chunk(const ImgDesc& d, uint32_t c, int t, bool need_px, ChunkPx& r) {
+  const uint64_t N = (uint64_t)d.H * d.W;
+  const uint64_t p0 = (uint64_t)c * SCAN_PX + (uint64_t)HIDE_PX * t;
+  r.valid = p0 < N ? (int)umin64(HIDE_PX, N - p0) : 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      G += sum;
-      if (EXTRACT) {
-        const uint32_t tl = (uint32_t)sw;
-        for (int j = 0; j <= L && have < 32; j++) {
-          const uint32_t vj = __shfl_sync(0xffffffffu, v, j), tj = __shfl_sync(0xffffffffu, tl, j);
-          const uint32_t fj = __shfl_sync(0xffffffffu, f, j);
-          if (fj == 2) {
-            acc |= have == 0 ? tj : (tj << have);
-            have = 32;
-          } else if (vj) {
-            const uint32_t nb = vj < 32 ? vj : 32;
-            const uint32_t part = nb == 32 ? tj : (tj & ((1u << nb) - 1u));
-            acc |= have == 0 ? part : (part << have);
-            have = have + vj > 32 ? 32 : have + vj;
-          }
-        }
-      }
-      if (incm) break;
-      cur -= 32;
+  for (int i = 0; i < 8; i++) r.px[i] = 0;
+  r.lbits = 0xFFFFFFFFu;
+  const bool lmr = d.variant == RDHEI_LMR;
+  if (need_px || !lmr) {
+    const uint8_t* src = d.src + p0;
+    if (r.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(src)), e = __ldcs(reinterpret_cast<const uint4*>(src + 16));
+      r.px[0] = a.x; r.px[1] = a.y; r.px[2] = a.z; r.px[3] = a.w;
+      r.px[4] = e.x; r.px[5] = e.y; r.px[6] = e.z; r.px[7] = e.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < HIDE_PX; k++)
+        if (k < r.valid) r.px[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
     }
-    uint32_t itail = 0;
-    if (EXTRACT) itail = T >= 32 ? tail : (T > 0 ? ((acc << T) | tail) : acc);
-    if (lane == 0) st_release_u64(st, pack_status(2, G + T, itail));
   }
-  G_out = G;
-  carry_out = acc;
+  if (lmr && r.valid > 0) r.lbits = stream_bits32(d.map_bits, (N + 31) >> 5, p0);
 }
 
-template <bool EXTRACT>
-__global__ void __launch_bounds__(HIDE_THREADS) k_scan(Batch B) {
-  __shared__ uint32_t sbuf[SBUF_WORDS];   // embed: e words of the chunk (MSB-first); extract: raw stream
-  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
-  __shared__ uint32_t s_ticket, s_G, s_carry;
-
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_ticket = atomicAdd(B.tickets + TK_HIDE, 1u);
-  if (EXTRACT)
-    for (int i = t; i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
-  __syncthreads();
-  const uint32_t g = s_ticket;
-  const int img = owner_of(B.chunk_prefix, B.n_images, g);
-  const ImgDesc& d = B.desc[img];
-  rdhei_info* info = reinterpret_cast<rdhei_info*>(d.info);
-  const uint64_t N = (uint64_t)d.H * d.W;
-  const uint32_t c = g - d.chunk_base;
-  const int b = d.b > 0 ? d.b : info->b;
-  const bool lmr = d.variant == RDHEI_LMR;
-  const uint32_t slots = lmr ? (uint32_t)(b - 1) : (uint32_t)b;
-  const uint32_t top = lmr ? 6u : 7u;
-  const uint32_t fshift = top + 1 - slots;                    // field's lowest bit position
-
-  // ---- my 32 pixels, their labels and slot count -----------------------------------
-  const uint64_t p0 = (uint64_t)c * SCAN_PX + (uint64_t)HIDE_PX * t;
-  const int valid = p0 < N ? (int)umin64(HIDE_PX, N - p0) : 0;
-  const uint8_t* src = d.src + p0;
-  uint32_t px[8];
-#pragma unroll
-  for (int i = 0; i < 8; i++) px[i] = 0;
-  if (valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-    const uint4 a = *reinterpret_cast<const uint4*>(src), e = *reinterpret_cast<const uint4*>(src + 16);
-    px[0] = a.x; px[1] = a.y; px[2] = a.z; px[3] = a.w; px[4] = e.x; px[5] = e.y; px[6] = e.z; px[7] = e.w;
-  } else {
-    for (int k = 0; k < valid; k++) px[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
-  }
-  uint32_t zmask;   // bit k: pixel k is redundant (label 0)
-  if (!lmr) {
-    zmask = 0;
+__device__ __forceinline__ uint32_t zero_mask(const ImgDesc& d, const ChunkPx& r) {
+  uint32_t z;
+  if (d.variant != RDHEI_LMR) {
+    z = 0;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      const uint32_t nib = (((~px[i]) & 0x01010101u) * 0x01020408u) >> 24;   // LSB == 0, pixel 4i+k -> bit k
-      zmask |= (nib & 0xFu) << (4 * i);
+      const uint32_t nib = (((~r.px[i]) & 0x01010101u) * 0x01020408u) >> 24;   // LSB == 0, pixel 4i+k -> bit k
+      z |= (nib & 0xFu) << (4 * i);
     }
   } else {
-    zmask = ~stream_bits32(d.map_bits, (N + 31) >> 5, p0);
+    z = ~r.lbits;
   }
-  if (valid < 32) zmask &= valid <= 0 ? 0u : ((1u << valid) - 1u);
-  const uint32_t mycnt = (uint32_t)__popc(zmask) * slots;
+  if (r.valid < 32) z &= r.valid <= 0 ? 0u : ((1u << r.valid) - 1u);
+  return z;
+}
 
-  // ---- block scan ------------------------------------------------------------------------
-  uint32_t inc = mycnt;
+__device__ __forceinline__ int slots_of(const ImgDesc& d, const rdhei_info* info) {
+  const int b = d.b > 0 ? d.b : info->b;
+  return d.variant == RDHEI_LMR ? b - 1 : b;
+}
+
+// PRMT selectors for the 4 pixels of a word with label-0 pattern z (bit q = pixel q):
+//   expand:  byte q <- byte rank(q) of the consecutive fields (4 = zero byte) if z_q;
+//   compact: byte j <- byte of the j-th label-0 pixel (4 = zero byte).
+__host__ __device__ __forceinline__ uint32_t sel_expand(uint32_t z) {
+  uint32_t sel = 0, r = 0;
+  for (int q = 0; q < 4; q++) {
+    const uint32_t nib = ((z >> q) & 1u) ? r++ : 4u;
+    sel |= nib << (4 * q);
+  }
+  return sel;
+}
+__host__ __device__ __forceinline__ uint32_t sel_compact(uint32_t z) {
+  uint32_t sel = 0x4444u, j = 0;
+  for (int q = 0; q < 4; q++)
+    if ((z >> q) & 1u) { sel = (sel & ~(0xFu << (4 * j))) | ((uint32_t)q << (4 * j)); j++; }
+  return sel;
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads); returns the
+// exclusive prefix and the block total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += v;
+    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
   if (lane == 31) warp_tot[warp] = inc;
   __syncthreads();
-  uint32_t wbase = 0, T = 0;
+  uint32_t base = 0, tot = 0;
 #pragma unroll
   for (int i = 0; i < HIDE_THREADS / 32; i++) {
-    const uint32_t v = warp_tot[i];
-    wbase += i < warp ? v : 0u;
-    T += v;
-  }
-  const uint32_t my_off = wbase + inc - mycnt;            // exclusive, local to the chunk
-
-  if (EXTRACT) {
-    // gather my slots into the chunk-local raw stream (32 bits at a time)
-    uint64_t acc = 0;
-    uint32_t nacc = 0, o = my_off;
-    uint32_t zm = zmask;
-    while (zm) {
-      const int k = __ffs(zm) - 1;
-      zm &= zm - 1;
-      const uint32_t field = (px[k >> 2] >> (8 * (k & 3) + fshift)) & ((1u << slots) - 1u);
-      acc = (acc << slots) | field;
-      nacc += slots;
-      if (nacc >= 32) {
-        nacc -= 32;
-        or_bits(sbuf, o, (uint32_t)(acc >> nacc), 32);
-        o += 32;
-      }
-    }
-    if (nacc) or_bits(sbuf, o, (uint32_t)acc & ((1u << nacc) - 1u), nacc);
-    __syncthreads();
-  }
-
-  // ---- offset of the chunk ---------------------------------------------------------------
-  if (warp == 0) {
-    uint32_t tail = 0;
-    if (EXTRACT && T > 0) tail = T >= 32 ? get_bits(sbuf, T - 32, 32) : get_bits(sbuf, 0, T);
-    uint32_t G, carry;
-    lookback<EXTRACT>(B, d, info, g, c, T, tail, G, carry);
-    if (lane == 0) { s_G = G; s_carry = carry; }
+    const uint32_t u = warp_tot[i];
+    base += i < warp ? u : 0u;
+    tot += u;
   }
   __syncthreads();
-  const uint64_t G = s_G, Gend = G + T;
-  const bool last = c + 1 == d.nchunks;
-  if (last && t == 0) {
+  total = tot;
+  return base + inc - v;
+}
+
+// Pass 1 of the payload scan: slot count of every chunk (persistent, grid-stride; the
+// next chunk's loads are in flight while the current one is reduced).
+__global__ void __launch_bounds__(HIDE_THREADS) k_count(Batch B) {
+  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(B.chunk_status);
+  uint32_t g = blockIdx.x;
+  if (g >= B.total_chunks) return;
+  int img = owner_of(B.chunk_prefix, B.n_images, g);
+  ChunkPx cur;
+  issue_chunk(B.desc[img], g - B.desc[img].chunk_base, t, false, cur);
+  while (g < B.total_chunks) {
+    const ImgDesc& d = B.desc[img];
+    const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+    const uint32_t gn = g + gridDim.x;
+    int imgn = img;
+    ChunkPx nxt;
+    if (gn < B.total_chunks) {
+      imgn = owner_of(B.chunk_prefix, B.n_images, gn);
+      issue_chunk(B.desc[imgn], gn - B.desc[imgn].chunk_base, t, false, nxt);
+    }
+    uint32_t v = (uint32_t)__popc(zero_mask(d, cur)) * (uint32_t)slots_of(d, info);
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) warp_tot[warp] = v;
+    __syncthreads();
+    if (t == 0) {
+      uint32_t T = 0;
+#pragma unroll
+      for (int i = 0; i < HIDE_THREADS / 32; i++) T += warp_tot[i];
+      cnt[g] = T;
+    }
+    __syncthreads();
+    g = gn;
+    img = imgn;
+    cur = nxt;
+  }
+}
+
+// Per image: exclusive prefix of the chunk counts (the bit offset at which each chunk's
+// slots start -- Sec. III-A-2's "concatenation" order), the image totals and, for the
+// extractor, clearing of the output words shared by two chunks.
+template <bool EXTRACT>
+__global__ void __launch_bounds__(HIDE_THREADS) k_offsets(Batch B) {
+  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
+  const int t = threadIdx.x;
+  const int img = blockIdx.x;
+  const ImgDesc& d = B.desc[img];
+  rdhei_info* info = reinterpret_cast<rdhei_info*>(d.info);
+  const uint32_t* cnt = reinterpret_cast<const uint32_t*>(B.chunk_status);
+  uint32_t* off = reinterpret_cast<uint32_t*>(B.chunk_status) + B.total_chunks;
+  const uint32_t base = d.chunk_base;
+  const uint64_t lim_words = EXTRACT ? (d.max_bits + 31) >> 5 : 0;
+  uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
+  uint32_t running = 0;
+  for (uint32_t c0 = 0; c0 < d.nchunks; c0 += HIDE_THREADS) {
+    const uint32_t c = c0 + t;
+    const uint32_t v = c < d.nchunks ? cnt[base + c] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(v, warp_tot, tot) + running;
+    if (c < d.nchunks) {
+      off[base + c] = ex;
+      if (EXTRACT && v) {
+        const uint64_t a = ex >> 5, e = (uint64_t)(ex + v) >> 5;
+        if ((ex & 31) && a < lim_words) out[a] = 0u;                 // shared with the previous chunk
+        if (((ex + v) & 31) && e < lim_words) out[e] = 0u;          // shared with the next chunk
+      }
+    }
+    running += tot;
+  }
+  if (t == 0) {
     if (EXTRACT) {
-      info->extracted = umin64(d.max_bits, Gend);
+      // the word holding the receiver's last requested bit may end inside a chunk
+      const uint64_t E = umin64(d.max_bits, running);
+      if ((E & 31) && (E >> 5) < lim_words) out[E >> 5] = 0u;
+      info->extracted = E;
     } else {
-      info->embedded = umin64(d.nbits, Gend);
-      if (d.nbits > Gend) { info->status = ERR_CAPACITY; set_error(B.err, ERR_CAPACITY); }
+      info->embedded = umin64(d.nbits, running);
+      if (d.nbits > running) { info->status = ERR_CAPACITY; set_error(B.err, ERR_CAPACITY); }
     }
   }
+}
 
-  if (!EXTRACT) {
-    // the K2-encrypted message words covering [G, min(Gend, nbits)), MSB-first
-    const uint64_t end = umin64(Gend, d.nbits);
-    const uint32_t* ew = reinterpret_cast<const uint32_t*>(d.ebuf);
-    const uint64_t w_lo = G >> 5;
-    const uint32_t nw = end > G ? (uint32_t)(((end - 1) >> 5) - w_lo + 1) : 0u;
-    for (uint32_t i = t; i < nw; i += HIDE_THREADS) sbuf[i] = bswap32(ew[w_lo + i]);
-    if (t == 0) sbuf[nw] = 0u;
-    __syncthreads();
-    if (zmask && G + my_off < d.nbits) {
-      uint64_t k = G + my_off;
-      const uint64_t base = 32 * w_lo;
-      uint32_t zm = zmask;
-      while (zm && k < d.nbits) {
-        const int q = __ffs(zm) - 1;
-        zm &= zm - 1;
-        const uint32_t n = (uint32_t)umin64(slots, d.nbits - k);
-        const uint32_t e = get_bits(sbuf, (uint32_t)(k - base), n);
-        const uint32_t bs = 8 * (q & 3) + (top + 1 - n);        // first bit into bit `top`
-        const uint32_t m = ((1u << n) - 1u) << bs;
-        px[q >> 2] = (px[q >> 2] & ~m) | (e << bs);
-        k += slots;
+// Pass 2 of the payload scan (persistent, grid-stride, next chunk prefetched).
+// Hider: the K2-encrypted message bits of each chunk's slot range go into its slots,
+// first bit into bit 7 (EMR) or 6 (LMR).  Receiver: the slots are concatenated; words
+// inside the chunk's range are stored, words shared with a neighbour are OR-ed (they
+// were cleared by k_offsets).
+template <bool EXTRACT>
+__global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
+  constexpr int EW = (SBUF_WORDS + HIDE_THREADS - 1) / HIDE_THREADS;   // message words per thread
+  __shared__ uint32_t sbuf[SBUF_WORDS];   // hider: e words (MSB-first); receiver: raw slot stream
+  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
+  __shared__ uint32_t s_expand[16], s_compact[16];
+  const int t = threadIdx.x;
+  if (t < 16) { s_expand[t] = sel_expand(t); s_compact[t] = sel_compact(t); }
+  __syncthreads();
+  const uint32_t* cnt = reinterpret_cast<const uint32_t*>(B.chunk_status);
+  const uint32_t* off = cnt + B.total_chunks;
+  uint32_t g = blockIdx.x;
+  if (g >= B.total_chunks) return;
+  int img = owner_of(B.chunk_prefix, B.n_images, g);
+  ChunkPx cur;
+  issue_chunk(B.desc[img], g - B.desc[img].chunk_base, t, true, cur);
+  uint64_t G = off[g];
+  uint32_t T = cnt[g];
+  while (g < B.total_chunks) {
+    const ImgDesc& d = B.desc[img];
+    const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+    const uint32_t slots = (uint32_t)slots_of(d, info);
+    const uint32_t top = d.variant == RDHEI_LMR ? 6u : 7u;
+    const uint32_t fshift = top + 1 - slots;
+    const uint32_t fmask = (1u << slots) - 1u;
+    const uint32_t c = g - d.chunk_base;
+    const uint64_t p0 = (uint64_t)c * SCAN_PX + (uint64_t)HIDE_PX * t;
+
+    // the message words of this chunk (hider), loads issued before the scan
+    uint32_t ew[EW];
+    uint64_t w_lo = G >> 5;
+    uint32_t nw = 0;
+    if (!EXTRACT) {
+      const uint64_t end = umin64(G + T, d.nbits);
+      nw = end > G ? (uint32_t)(((end - 1) >> 5) - w_lo + 1) : 0u;
+      const uint32_t* e = reinterpret_cast<const uint32_t*>(d.ebuf) + w_lo;
+#pragma unroll
+      for (int i = 0; i < EW; i++) {
+        const uint32_t k = t + i * HIDE_THREADS;
+        ew[i] = k < nw ? __ldcs(e + k) : 0u;
       }
     }
-    uint8_t* dst = d.dst + p0;
-    if (valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-      reinterpret_cast<uint4*>(dst)[0] = make_uint4(px[0], px[1], px[2], px[3]);
-      reinterpret_cast<uint4*>(dst)[1] = make_uint4(px[4], px[5], px[6], px[7]);
-    } else {
-      for (int k = 0; k < valid; k++) dst[k] = (uint8_t)(px[k >> 2] >> (8 * (k & 3)));
+    // next chunk in flight
+    const uint32_t gn = g + gridDim.x;
+    int imgn = img;
+    ChunkPx nxt;
+    uint64_t Gn = 0;
+    uint32_t Tn = 0;
+    if (gn < B.total_chunks) {
+      imgn = owner_of(B.chunk_prefix, B.n_images, gn);
+      issue_chunk(B.desc[imgn], gn - B.desc[imgn].chunk_base, t, true, nxt);
+      Gn = off[gn];
+      Tn = cnt[gn];
     }
-  } else {
-    // raw output words whose last bit lies in this chunk (the image's last chunk also
-    // writes the final partial word), zero past min(max_bits, Gend)
-    const uint64_t limit = umin64(d.max_bits, Gend);
-    const uint64_t w_lo = G >> 5;
-    uint64_t hi_excl = Gend >> 5;
-    if (last && (Gend & 31)) hi_excl += 1;
-    const uint64_t lim = (d.max_bits + 31) >> 5;
-    if (hi_excl > lim) hi_excl = lim;
-    uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
-    const uint32_t carry = s_carry;
-    for (uint64_t w = w_lo + t; w < hi_excl; w += HIDE_THREADS) {
-      const uint64_t b0 = 32 * w;
-      uint32_t raw;
-      if (b0 >= G) {
-        raw = get_bits(sbuf, (uint32_t)(b0 - G), 32);
+
+    const uint32_t zmask = zero_mask(d, cur);
+    uint32_t Tb;
+    const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, warp_tot, Tb);
+
+    if (!EXTRACT) {
+#pragma unroll
+      for (int i = 0; i < EW; i++) {
+        const uint32_t k = t + i * HIDE_THREADS;
+        if (k < nw) sbuf[k] = bswap32(ew[i]);
+      }
+      if (t == 0) sbuf[nw] = 0u;
+      __syncthreads();
+      if (zmask && G + my_off < d.nbits) {
+        // per 4-pixel word: read the word's slots at once, spread the fields to
+        // consecutive bytes, then move them to their pixels with one byte permute
+        const uint64_t base = 32 * w_lo;
+        const uint32_t FREP = (fmask << fshift) * 0x01010101u;
+        const uint32_t s2 = 2 * slots, s3 = 3 * slots;
+        uint64_t k = G + my_off;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
+          const uint32_t nb = (uint32_t)__popc(zw) * slots;         // <= 28 bits
+          if (nb && k < d.nbits) {
+            const uint32_t avail = (uint32_t)umin64(nb, d.nbits - k);
+            const uint32_t E = get_bits(sbuf, (uint32_t)(k - base), avail) << (32 - avail);   // left-aligned
+            const uint32_t rs = 32 - slots;
+            const uint32_t cons = (E >> rs) | (((E << slots) >> rs) << 8) | (((E << s2) >> rs) << 16) |
+                                  (((E << s3) >> rs) << 24);
+            const uint32_t zb = ((zw * 0x00204081u) & 0x01010101u) * 0xFFu;   // label-0 bytes
+            uint32_t m = zb & FREP;
+            if (avail < nb) {
+              // the message ends inside this word: only its first `avail` slot bits
+              uint32_t part = 0, left = avail;
+              for (int j = 0; j < 4; j++) {
+                const uint32_t n = left < slots ? left : slots;
+                part |= (fmask & ~(fmask >> n)) << (8 * j);
+                left -= n;
+              }
+              m &= __byte_perm(part << fshift, 0, s_expand[zw]);
+            }
+            cur.px[i] = (cur.px[i] & ~m) | (__byte_perm(cons << fshift, 0, s_expand[zw]) & m);
+          }
+          k += nb;
+        }
+      }
+      uint8_t* dst = d.dst + p0;
+      if (cur.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+        __stcs(reinterpret_cast<uint4*>(dst), make_uint4(cur.px[0], cur.px[1], cur.px[2], cur.px[3]));
+        __stcs(reinterpret_cast<uint4*>(dst) + 1, make_uint4(cur.px[4], cur.px[5], cur.px[6], cur.px[7]));
       } else {
-        const uint32_t k = (uint32_t)(G - b0);             // 1..31 bits from earlier chunks
-        raw = ((carry & ((1u << k) - 1u)) << (32 - k)) | (sbuf[0] >> k);
+#pragma unroll
+        for (int k = 0; k < HIDE_PX; k++)
+          if (k < cur.valid) dst[k] = (uint8_t)(cur.px[k >> 2] >> (8 * (k & 3)));
       }
-      if (b0 + 32 > limit) {
-        const uint64_t keep = limit > b0 ? limit - b0 : 0;
-        raw = keep == 0 ? 0u : (raw & (0xFFFFFFFFu << (32 - keep)));
+    } else {
+      for (int i = t; i < (int)((Tb >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
+      __syncthreads();
+      // gather my slots into the chunk-local stream: per 4-pixel word one byte permute
+      // packs the fields of its label-0 pixels into consecutive bytes, which are then
+      // concatenated and appended 32 bits at a time
+      {
+        uint64_t acc = 0;
+        uint32_t nacc = 0, o = my_off;
+        const uint32_t FREP = fmask * 0x01010101u;
+        const uint32_t s2 = 2 * slots, s3 = 3 * slots;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
+          const uint32_t cnt = (uint32_t)__popc(zw);
+          const uint32_t cb = __byte_perm(cur.px[i] >> fshift, 0, s_compact[zw]) & FREP;
+          const uint32_t full = ((cb & 0xFFu) << s3) | (((cb >> 8) & 0xFFu) << s2) |
+                                (((cb >> 16) & 0xFFu) << slots) | (cb >> 24);
+          const uint32_t nb = cnt * slots;
+          const uint32_t chunk = full >> ((4 - cnt) * slots);
+          acc = (acc << nb) | chunk;
+          nacc += nb;
+          if (nacc >= 32) {
+            nacc -= 32;
+            or_bits(sbuf, o, (uint32_t)(acc >> nacc), 32);
+            o += 32;
+          }
+        }
+        if (nacc) or_bits(sbuf, o, (uint32_t)acc & ((1u << nacc) - 1u), nacc);
       }
-      out[w] = bswap32(raw);
+      __syncthreads();
+      // words of [G, min(G + T, E)), E = bits the receiver asked for and the image holds
+      const uint64_t E = info->extracted;
+      const uint64_t end = umin64(G + T, E);
+      uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
+      if (end > G) {
+        const uint64_t w_hi = (end - 1) >> 5;
+        for (uint64_t w = w_lo + t; w <= w_hi; w += HIDE_THREADS) {
+          const uint64_t b0 = 32 * w;
+          const uint64_t lo = b0 > G ? b0 : G, hi = b0 + 32 < end ? b0 + 32 : end;   // my bits of word w
+          uint32_t raw = get_bits(sbuf, (uint32_t)(lo - G), (uint32_t)(hi - lo));
+          raw <<= (uint32_t)(b0 + 32 - hi);
+          if (lo == b0 && hi == b0 + 32) out[w] = bswap32(raw);
+          else atomicOr(out + w, bswap32(raw));
+        }
+      }
     }
+    __syncthreads();   // sbuf is rewritten by the next chunk
+    g = gn;
+    img = imgn;
+    cur = nxt;
+    G = Gn;
+    T = Tn;
   }
 }
 
@@ -337,10 +441,27 @@ __global__ void k_lmr_side(Batch B) {
   for (int k = 0; k < n; k++) d.dst[p0 + k] = (uint8_t)((d.dst[p0 + k] & 0x7Fu) | (((sb >> k) & 1u) << 7));
 }
 
+// one resident wave of a persistent kernel (CTAs per SM from the occupancy calculator)
+template <typename K>
+static int persistent_grid(K kernel, uint32_t work) {
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, HIDE_THREADS, 0);
+  const uint32_t g = (uint32_t)(sms > 0 ? sms : 1) * (uint32_t)(per_sm > 0 ? per_sm : 1);
+  return (int)(work < g ? work : g);
+}
+// count + per-image offsets
+void launch_count(const Batch& B, bool extract, cudaStream_t st) {
+  if (B.total_chunks == 0) return;
+  k_count<<<persistent_grid(k_count, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
+  if (extract) k_offsets<true><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
+  else k_offsets<false><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
+}
 void launch_scan(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
-  if (extract) k_scan<true><<<B.total_chunks, HIDE_THREADS, 0, st>>>(B);
-  else k_scan<false><<<B.total_chunks, HIDE_THREADS, 0, st>>>(B);
+  if (extract) k_scan<true><<<persistent_grid(k_scan<true>, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
+  else k_scan<false><<<persistent_grid(k_scan<false>, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
 }
 void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st) {
   if (B.total_z2_blocks == 0) return;

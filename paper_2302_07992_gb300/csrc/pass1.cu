@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 #pragma unroll
         for (int q = 0; q < 4; q++) s4[q] = make_uint4(sw[4 * q], sw[4 * q + 1], sw[4 * q + 2], sw[4 * q + 3]);
       } else {
-        for (int c = 0; c < len; c++) st[c] = (uint8_t)(sw[c >> 2] >> (8 * (c & 3)));
+#pragma unroll
+        for (int c = 0; c < 64; c++)
+          if (c < len) st[c] = (uint8_t)(sw[c >> 2] >> (8 * (c & 3)));
       }
     }
     // label histogram: zeros(b) = #pixels whose top b bits equal the left neighbour's
@@ -207,7 +209,9 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 #pragma unroll
         for (int q = 0; q < 4; q++) s4[q] = make_uint4(px[4 * q], px[4 * q + 1], px[4 * q + 2], px[4 * q + 3]);
       } else {
-        for (int c = 0; c < len; c++) st[c] = (uint8_t)(px[c >> 2] >> (8 * (c & 3)));
+#pragma unroll
+        for (int c = 0; c < 64; c++)
+          if (c < len) st[c] = (uint8_t)(px[c >> 2] >> (8 * (c & 3)));
       }
     }
     reinterpret_cast<uint64_t*>(B.aux + (size_t)g * AUX_BYTES)[r] = auxbits;
