@@ -166,6 +166,27 @@ int rdhei_plan_stage_count(int op);
 const char *rdhei_stage_name(int op, int stage);
 int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Extraction without any allocation.  The paper has no counterpart to this call; it
+ * exists for callers that cannot allocate device memory at all -- code that runs in a
+ * host callback or under a runtime that owns every allocation, or a tool that links
+ * only this library -- and so cannot hand rdhei_extract a workspace.  It does what
+ * rdhei_extract does for ONE image (job->src, job->map_bits for LMR, job->bits_out,
+ * job->max_bits, job->info, job->b, K2) with the kernels rdhei_extract uses, and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Scratch: a file-scope device array of about 17 KB that the CUDA runtime sets up
+ *     when the library loads; every GPU that loads the library holds it until exit.
+ *   Limit: H * W <= RDHEI_NOALLOC_MAX_PIXELS (2^24); larger images return
+ *     RDHEI_ESPACE before any GPU work.
+ *   First call on a device: looks the array's device address up (cudaGetSymbolAddress
+ *     with that device current) and caches it; make it before any stream capture.
+ *   Sharing: every call uses the same array and it keeps the last call's contents;
+ *     what must start at zero is cleared on each call.  Calls whose work overlaps on
+ *     the GPU (other streams, other threads) race: order them on one stream.
+ *   Returns RDHEI_EINVAL for bad arguments, RDHEI_ECUDA for a failed CUDA call. */
+#define RDHEI_NOALLOC_MAX_PIXELS (1u << 24)
+int rdhei_extract_noalloc(const rdhei_job *job, void *stream);
+
 /* Workspace-wide device error word of the most recent call on this workspace
  * (synchronises the stream).  0 = no error, else an rdhei_status code. */
 int rdhei_workspace_status(void *ws, void *stream, int32_t *code);

@@ -290,3 +290,16 @@ def lmr_set_side(enc: torch.Tensor, p: Params, side_bits: torch.Tensor, side_nbi
     j = make_job(p, H, W, dst=out, side_bits=as_bitbuf(side_bits, side_nbits), side_nbits=side_nbits, info=info)
     run_jobs(OP_LMR_SET_SIDE, [j], stream)
     return out
+
+
+# ------------------------------------------------------- allocation-free extract --
+_lib.rdhei_extract_noalloc.argtypes = [_JobP, ctypes.c_void_p]
+_lib.rdhei_extract_noalloc.restype = ctypes.c_int
+NOALLOC_MAX_PIXELS = 1 << 24
+
+
+def extract_noalloc_job(job: Job, stream=None) -> int:
+    """rdhei_extract_noalloc on one prepared job; returns the C status code.  For
+    callers that cannot allocate device memory: the library uses a static device
+    array instead of a workspace (one image, at most NOALLOC_MAX_PIXELS pixels)."""
+    return int(_lib.rdhei_extract_noalloc(ctypes.byref(job), _stream(stream)))
