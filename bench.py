@@ -62,6 +62,29 @@ def side_nbits(H, W):
     return (H * W + 7) // 8
 
 
+# ----------------------------------------------------------- replicas (N > 1) --
+def rank_images(rank: int, n_per_rank: int) -> range:
+    """Global image indices of one rank: each replica works on its own batch (weak
+    scaling), so ranks never share an image and no data crosses between GPUs."""
+    return range(rank * n_per_rank, (rank + 1) * n_per_rank)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Step time of the job = the slowest rank's (the only collective of the path)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_throughput(px_per_rank_step: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job Mpixel/s: pixels all ranks processed / slowest rank's time."""
+    return px_per_rank_step * world * steps / (max_ms / 1e3) / 1e6
+
+
 # --------------------------------------------------------------- oracle arm --
 def _oracle_pipeline(args):
     """Full oracle pipeline on one image; returns (pixels, seconds)."""
@@ -157,7 +180,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     n, H, W = args.images, args.size, args.size
     N = H * W
-    first = rank * n
+    first = rank_images(rank, n).start
     imgs_np = args._images
     variants = [rd.EMR if (first + k) % 2 == 0 else rd.LMR for k in range(n)]
     params = []
@@ -257,13 +280,9 @@ def run_gpu(args, rank, world, local_rank):
         for i, (_, op, s, name) in enumerate(stage_list):
             t0 = start if (k == 0 and i == 0) else (evs[k][i - 1] if i > 0 else evs[k - 1][-1])
             per_stage.setdefault(name, []).append(t0.elapsed_time(evs[k][i]))
-    ms = [total_ms]
-    if world > 1:
-        t = torch.tensor(ms, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t[0])
+    total_ms = max_over_ranks(total_ms, world, dev)
     px_step = n * N
-    value = px_step * world * K / (total_ms / 1e3) / 1e6
+    value = job_throughput(px_step, world, K, total_ms)
 
     # end to end through the public API with host buffers: H2D inputs, four calls,
     # D2H results, every step
@@ -299,18 +318,13 @@ def run_e2e(args, rd, torch, dev, stream, stage_list, imgs, payload, rec, bits_o
         one()
     b.record(stream)
     torch.cuda.synchronize(dev)
-    ms = a.elapsed_time(b)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(a.elapsed_time(b), world, dev)
     px = imgs.shape[0] * imgs.shape[1] * imgs.shape[2]
     h2d = h_img.numel() + h_pay.numel()
     d2h = h_rec.numel() + h_bits.numel()
     # results read back must still be the verified ones
     assert torch.equal(h_rec, rec.cpu())
-    return {"value": px * world * K / (ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    return {"value": job_throughput(px, world, K, ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": K}
 
 
@@ -457,7 +471,7 @@ def main():
         return
 
     # images are drawn before CUDA is touched (spawned pool)
-    args._images = make_images(args.images, args.size, args.size, first=rank * args.images)
+    args._images = make_images(args.images, args.size, args.size, first=rank_images(rank, args.images).start)
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_base = oracle_throughput(args._images, 0, budget_s=10.0)
