@@ -110,7 +110,9 @@ def oracle_throughput(images, first, budget_s=15.0):
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0))
-    # calibrate on one image, then size the sample to ~budget_s of wall time
+    # calibrate on one image (after a first call that loads the library), then size
+    # the sample to ~budget_s of wall time
+    _oracle_pipeline((images[0], first, 0))
     _, t1 = _oracle_pipeline((images[0], first, 0))
     per_core = max(1, int(budget_s / max(t1, 1e-3)))
     n = min(len(images), per_core * cores)
@@ -419,9 +421,41 @@ def roofline(res, peaks, args):
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["hbm_frac"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(dom, px)
+    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    roof["algorithmic_bytes"] = hbm_bytes.get(dom, 0.0)
     roof["avg_launch_ms"] = avg_ms
     return roof, out_all
+
+
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources and the ABI header (staleness check of profile data)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2302_07992_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_2302_07992_gb300", "csrc", "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "rdhei.h"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, px_per_launch: int):
+    """DRAM bytes per launch from the committed ncu capture, scaled by pixels; None when
+    the kernels changed after the capture or the kernel was not captured."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_batch600x512.json")
+    try:
+        with open(path) as f:
+            doc = json.load(f)
+    except Exception:
+        return None
+    if doc.get("source_hash") != kernel_source_hash():
+        return None
+    k = doc.get("kernels", {}).get(kernel)
+    return None if k is None else k["dram_bytes_per_px"] * px_per_launch
 
 
 def load_peaks():
