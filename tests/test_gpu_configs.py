@@ -1,0 +1,143 @@
+"""GPU parity on the workload shapes of the benchmark configurations, through the
+batched (plan) path: many images of uneven sizes and both variants in one launch per
+operation, each image's outputs equal to the CPU oracle's byte for byte.
+
+  * 512 x 512 batch with per-image smoothness, EMR and LMR mixed;
+  * uneven sizes drawn from {256, ..., 4096} per axis plus ragged sides;
+  * the largest size, 8192 x 8192;
+  * decode-only on 4096 x 4096 images marked by the oracle (GPU receivers on inputs the
+    GPU did not produce).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_07992_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rd():
+    from paper_2302_07992_gb300 import rdhei
+    return rdhei
+
+
+def _keys(seed):
+    k = synth.keys(seed)
+    return dict(k1=k["k1"], nonce1=k["nonce1"], k2=k["k2"], nonce2=k["nonce2"])
+
+
+def _bits(t, n):
+    return t.detach().cpu().numpy()[: (n + 7) // 8]
+
+
+def _run_batch(rd, imgs, variants, seeds, side_frac=0.125):
+    """All four operations, one plan (one launch sequence) per operation."""
+    n = len(imgs)
+    P = [rd.Params(variant=v, **_keys(s)) for v, s in zip(variants, seeds)]
+    d_img = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    enc = [torch.empty_like(x) for x in d_img]
+    marked = [torch.empty_like(x) for x in d_img]
+    rec = [torch.empty_like(x) for x in d_img]
+    N = [im.size for im in imgs]
+    maps = [rd.bitbuf(N[i]) for i in range(n)]
+    etas = [rd.bitbuf(N[i]) for i in range(n)]
+    side_n = [int(N[i] * side_frac) if variants[i] == rd.LMR else 0 for i in range(n)]
+    side_np = [synth.random_bits(seeds[i], side_n[i]) if side_n[i] else None for i in range(n)]
+    sides = [rd.as_bitbuf(torch.from_numpy(side_np[i]), side_n[i]) if side_n[i] else None for i in range(n)]
+    info = rd.new_info(n)
+    jobs = [rd.make_job(P[i], *imgs[i].shape, src=d_img[i], dst=enc[i], map_bits=maps[i],
+                        eta_bits=etas[i] if variants[i] == rd.LMR else None, side_bits=sides[i], side_nbits=side_n[i],
+                        info=info[i]) for i in range(n)]
+    rd.Plan(jobs).run(rd.OP_LABEL_ENCRYPT)
+    torch.cuda.synchronize()
+    inf = rd.read_info(info)
+    caps = [r["capacity"] for r in inf]
+    pays = [synth.payload_bits(seeds[i], caps[i]) for i in range(n)]
+    d_pay = [rd.as_bitbuf(torch.from_numpy(pays[i]), caps[i]) for i in range(n)]
+    bits = [rd.bitbuf(caps[i]) for i in range(n)]
+    lm = [maps[i] if variants[i] == rd.LMR else None for i in range(n)]
+    rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=enc[i], dst=marked[i], map_bits=lm[i], payload=d_pay[i],
+                         nbits=caps[i], info=info[i], b=0) for i in range(n)]).run(rd.OP_EMBED)
+    rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=marked[i], map_bits=lm[i], bits_out=bits[i], max_bits=caps[i],
+                         info=info[i], b=0) for i in range(n)]).run(rd.OP_EXTRACT)
+    rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=marked[i], dst=rec[i], map_bits=lm[i],
+                         eta_bits=etas[i] if variants[i] == rd.LMR else None, info=info[i], b=0)
+             for i in range(n)]).run(rd.OP_DECRYPT_RECOVER)
+    torch.cuda.synchronize()
+    return dict(P=P, enc=enc, marked=marked, rec=rec, maps=maps, etas=etas, bits=bits, info=rd.read_info(info),
+                caps=caps, pays=pays, side_np=side_np, side_n=side_n)
+
+
+def _check_against_oracle(rd, imgs, variants, seeds, out, i):
+    img, v = imgs[i], variants[i]
+    op = oracle.Params(variant=v, **_keys(seeds[i]))
+    H, W = img.shape
+    r = oracle.label_encrypt(op, img, out["side_np"][i], out["side_n"][i])
+    g = out["info"][i]
+    assert g["hist"] == [int(x) for x in r.hist] and g["b"] == r.b and g["capacity"] == r.capacity, i
+    assert np.array_equal(out["enc"][i].cpu().numpy(), r.enc), i
+    assert np.array_equal(_bits(out["maps"][i], H * W), r.map_bits), i
+    lm = r.map_bits if v == oracle.LMR else None
+    mref, k = oracle.embed(op, r.b, r.enc, out["pays"][i], r.capacity, lm)
+    assert np.array_equal(out["marked"][i].cpu().numpy(), mref), i
+    xref, xk = oracle.extract(op, r.b, mref, r.capacity, lm)
+    assert g["extracted"] == xk and np.array_equal(_bits(out["bits"][i], xk), xref), i
+    rref = oracle.decrypt_recover(op, r.b, mref, lm, r.eta_bits if v == oracle.LMR else None)
+    assert np.array_equal(out["rec"][i].cpu().numpy(), rref), i
+
+
+def test_batch_512_mixed_variants(rd):
+    n = 24
+    imgs = [synth.batch_image(2, k, 512, 512, vary=True) for k in range(n)]
+    variants = [rd.EMR if k % 2 == 0 else rd.LMR for k in range(n)]
+    seeds = [synth.image_seed(2, k) for k in range(n)]
+    out = _run_batch(rd, imgs, variants, seeds)
+    for i in range(n):
+        _check_against_oracle(rd, imgs, variants, seeds, out, i)
+
+
+def test_uneven_sizes_one_launch(rd):
+    rng = np.random.default_rng(33)
+    sides = [256, 512, 1024, 2048]
+    shapes = [(int(rng.choice(sides)), int(rng.choice(sides))) for _ in range(8)]
+    shapes += [(4096, 256), (1000, 777), (333, 2048), (4096, 4096)]
+    imgs = [synth.synth_image(H, W, 100 + i) for i, (H, W) in enumerate(shapes)]
+    variants = [rd.EMR if i % 3 else rd.LMR for i in range(len(shapes))]
+    seeds = [500 + i for i in range(len(shapes))]
+    out = _run_batch(rd, imgs, variants, seeds)
+    for i in range(len(shapes)):
+        _check_against_oracle(rd, imgs, variants, seeds, out, i)
+
+
+@pytest.mark.slow
+def test_largest_size_8192(rd):
+    """8192 x 8192 (13 rotation levels, 16,384 tiles, 8,192 chunks), EMR, full parity."""
+    img = synth.synth_image(8192, 8192, 81)
+    out = _run_batch(rd, [img], [rd.EMR], [81])
+    _check_against_oracle(rd, [img], [rd.EMR], [81], out, 0)
+
+
+def test_decode_only_on_oracle_marked_4096(rd):
+    """The GPU receivers on 4096 x 4096 images that the oracle encoded and marked."""
+    n = 2
+    for i in range(n):
+        img = synth.synth_image(4096, 4096, 900 + i)
+        v = oracle.EMR if i == 0 else oracle.LMR
+        op = oracle.Params(variant=v, **_keys(900 + i))
+        r = oracle.label_encrypt(op, img)
+        pay = synth.payload_bits(900 + i, r.capacity)
+        lm = r.map_bits if v == oracle.LMR else None
+        mref, _ = oracle.embed(op, r.b, r.enc, pay, r.capacity, lm)
+        p = rd.Params(variant=v, **_keys(900 + i))
+        dm = torch.from_numpy(mref).cuda()
+        dmap = rd.as_bitbuf(torch.from_numpy(r.map_bits), img.size) if lm is not None else None
+        deta = rd.as_bitbuf(torch.from_numpy(r.eta_bits), img.size) if lm is not None else None
+        x = rd.extract(dm, p, r.b, r.capacity, dmap)
+        xref, xk = oracle.extract(op, r.b, mref, r.capacity, lm)
+        assert x["extracted"] == xk and np.array_equal(_bits(x["bits"], xk), xref)
+        rec = rd.decrypt_recover(dm, p, r.b, dmap, deta)
+        rref = oracle.decrypt_recover(op, r.b, mref, lm, r.eta_bits if lm is not None else None)
+        assert np.array_equal(rec.cpu().numpy(), rref)
