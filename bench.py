@@ -372,6 +372,80 @@ def verify_batch(args, rd, imgs, enc, marked, rec, maps, etas, payload, bits_out
             "b_hist": {str(b): sum(1 for r in inf if r["b"] == b) for b in range(2, 9) if any(r["b"] == b for r in inf)}}
 
 
+# ------------------------------------------------- uneven batch: graph vs per-image --
+C3_SIDES = (256, 512, 1024, 2048, 4096)
+
+
+def c3_shapes(n_small=256, n_big=4, seed=3):
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.choice(C3_SIDES)), int(rng.choice(C3_SIDES))) for _ in range(n_small)]
+    return shapes + [(8192, 8192)] * n_big
+
+
+def _gen_shape(args):
+    k, H, W = args
+    return synth.synth_image(H, W, synth.image_seed(BASE_SEED + 1, k))
+
+
+def run_c3(args):
+    """Uneven batch (256 images, sides drawn from {256..4096} per axis, plus 4 x 8192^2):
+    the batched plans replayed as one CUDA graph vs per-image plain launches, same
+    outputs bit for bit."""
+    import torch
+    from paper_2302_07992_gb300 import pipeline as pp
+    from paper_2302_07992_gb300 import rdhei as rd
+    shapes = c3_shapes(args.c3_small, args.c3_big)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
+        imgs = pool.map(_gen_shape, [(k, H, W) for k, (H, W) in enumerate(shapes)], chunksize=2)
+    seeds = [synth.image_seed(BASE_SEED + 1, k) for k in range(len(shapes))]
+    variants = [rd.EMR if k % 2 == 0 else rd.LMR for k in range(len(shapes))]
+    params = []
+    for k in range(len(shapes)):
+        kk = synth.keys(seeds[k])
+        params.append(rd.Params(variant=variants[k], k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"]))
+    torch.cuda.set_device(0)
+    s = pp.ImageSet(imgs, variants, params)
+    bp = pp.BatchedPipeline(s, pp.default_payload(lambda i: seeds[i]))
+    px = s.pixels()
+
+    def timed(fn, K):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K
+
+    bp.capture()
+    ms_graph = timed(bp.replay, args.steps)
+    ref_rec = [x.clone() for x in s.rec]
+    ref_bits = [x.clone() for x in s.bits]
+    ms_batched = timed(bp.step, args.steps)
+    pi = pp.PerImagePipeline(s)
+    for x in s.rec:
+        x.zero_()
+    ms_per_image = timed(pi.step, max(3, args.steps // 4))
+    same = all(torch.equal(a, b) for a, b in zip(ref_rec, s.rec)) and \
+        all(torch.equal(a, b) for a, b in zip(ref_bits, s.bits))
+    lossless = all(torch.equal(s.rec[i], s.img[i]) for i in range(s.n) if variants[i] == rd.LMR)
+    return {"metric": METRIC, "value": px / (ms_graph / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"uneven batch: {args.c3_small} images with H, W drawn from {list(C3_SIDES)} "
+                                   f"+ {args.c3_big} x 8192x8192, EMR/LMR alternating, full-capacity payload",
+                       "pixels": px},
+            "batching": {"graph_batched_mpx": px / (ms_graph / 1e3) / 1e6,
+                         "eager_batched_mpx": px / (ms_batched / 1e3) / 1e6,
+                         "per_image_plain_mpx": px / (ms_per_image / 1e3) / 1e6,
+                         "launches_batched": bp.launches_per_step(), "launches_per_image": pi.launches_per_step(),
+                         "outputs_equal": bool(same), "lmr_lossless": bool(lossless)}}
+
+
 # ----------------------------------------------------------------- roofline --
 ALU_LANES_PER_SM = 64          # integer/logic pipe lanes per SM (4 sub-partitions x 16)
 SMS = 152
@@ -478,6 +552,10 @@ def main():
     ap.add_argument("--parity-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
+                    help="c2: the 1000-image 512x512 batch (default); c3: uneven batch, graph vs per-image")
+    ap.add_argument("--c3-small", type=int, default=256)
+    ap.add_argument("--c3-big", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -490,6 +568,11 @@ def main():
               "images_per_gpu": args.images, "H": args.size, "W": args.size,
               "keystream": "ChaCha20 (RFC 8439)", "parallelism": f"replicas x{args.gpus}",
               "l2": "no flush: each step streams ~1.6 GB (inputs and outputs > 129 MB L2)"}
+
+    if args.config == "c3" and args.impl == "gb300":
+        if rank == 0:
+            print(json.dumps(run_c3(args)))
+        return
 
     if args.impl == "reference":
         if rank != 0:
