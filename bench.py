@@ -446,6 +446,64 @@ def run_c3(args):
                          "outputs_equal": bool(same), "lmr_lossless": bool(lossless)}}
 
 
+# ------------------------------------------------------------------ serving --
+def run_c5(args):
+    """Poisson stream of mixed encode / decode requests (image sides log-uniform in
+    256..4096) through the continuous-batching server under a 40 GB device-memory
+    budget; p50 / p99 latency (arrival -> results in host memory) and sustained
+    Mpixel/s, at the configured rate and at twice it."""
+    import torch
+    from paper_2302_07992_gb300 import rdhei as rd
+    from paper_2302_07992_gb300 import serve as sv
+    rng = np.random.default_rng(5)
+    n_pool = args.c5_pool
+    sides = np.exp(rng.uniform(np.log(256), np.log(4096), size=(n_pool, 2))).astype(int)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
+        pool_imgs = pool.map(_gen_shape, [(10_000 + k, int(h), int(w)) for k, (h, w) in enumerate(sides)], chunksize=2)
+    torch.cuda.set_device(0)
+    # pre-encoded inputs for decode requests: marked images + maps, from one served pass
+    base = []
+    for k, img in enumerate(pool_imgs):
+        kk = synth.keys(20_000 + k)
+        p = rd.Params(variant=rd.EMR if k % 2 == 0 else rd.LMR, k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"],
+                      nonce2=kk["nonce2"])
+        nbits = img.size // 2
+        base.append(sv.Request(rid=k, kind="encode", params=p, image=torch.from_numpy(img).pin_memory(),
+                               payload=torch.from_numpy(synth.payload_bits(20_000 + k, nbits)).pin_memory(),
+                               nbits=nbits))
+    pre = {r.rid: r for r in sv.Server().run(base, realtime=False)}
+    results = {}
+    for mult in (1.0, 2.0):
+        rate = args.c5_rate * mult
+        n = int(rate * args.c5_seconds)
+        t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        reqs = []
+        for i in range(n):
+            k = int(rng.integers(n_pool))
+            b = base[k]
+            if rng.random() < 0.5:
+                reqs.append(sv.Request(rid=i, kind="encode", params=b.params, image=b.image, payload=b.payload,
+                                       nbits=b.nbits, arrival=float(t[i])))
+            else:
+                pr = pre[k].result
+                reqs.append(sv.Request(rid=i, kind="decode", params=b.params, image=pr["marked"],
+                                       nbits=pr["info"]["embedded"], b=pr["info"]["b"], lmr_map=pr.get("map_bits"),
+                                       lmr_eta=pr.get("eta_bits"), arrival=float(t[i])))
+        done = sv.Server(budget_bytes=40e9).run(reqs, realtime=True)
+        st = sv.latency_stats(done)
+        st["offered_req_s"] = rate
+        st["offered_mpx_s"] = sum(r.pixels for r in reqs) / args.c5_seconds / 1e6
+        results[f"x{mult:g}"] = st
+    first = results["x1"]
+    return {"metric": "p50/p99 request latency (arrival -> results on host)", "value": first["p99_ms"],
+            "unit": "ms (p99)", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": None,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.c5_rate:g} req/s for {args.c5_seconds:g} s, 50/50 encode/decode, "
+                                   f"sides log-uniform 256..4096 ({n_pool} distinct images), 40 GB budget"},
+            "serving": results}
+
+
 # ----------------------------------------------------------------- roofline --
 ALU_LANES_PER_SM = 64          # integer/logic pipe lanes per SM (4 sub-partitions x 16)
 SMS = 152
@@ -552,8 +610,12 @@ def main():
     ap.add_argument("--parity-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3"],
-                    help="c2: the 1000-image 512x512 batch (default); c3: uneven batch, graph vs per-image")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2: the 1000-image 512x512 batch (default); c3: uneven batch, graph vs per-image; "
+                         "c5: serving latency")
+    ap.add_argument("--c5-rate", type=float, default=2000.0)
+    ap.add_argument("--c5-seconds", type=float, default=5.0)
+    ap.add_argument("--c5-pool", type=int, default=64)
     ap.add_argument("--c3-small", type=int, default=256)
     ap.add_argument("--c3-big", type=int, default=4)
     args = ap.parse_args()
@@ -569,9 +631,9 @@ def main():
               "keystream": "ChaCha20 (RFC 8439)", "parallelism": f"replicas x{args.gpus}",
               "l2": "no flush: each step streams ~1.6 GB (inputs and outputs > 129 MB L2)"}
 
-    if args.config == "c3" and args.impl == "gb300":
+    if args.config in ("c3", "c5") and args.impl == "gb300":
         if rank == 0:
-            print(json.dumps(run_c3(args)))
+            print(json.dumps(run_c3(args) if args.config == "c3" else run_c5(args)))
         return
 
     if args.impl == "reference":
