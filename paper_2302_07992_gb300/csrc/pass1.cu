@@ -218,21 +218,39 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   }
 
   // ---- block sums of s at levels 1..6 -------------------------------------------------
-  // rp: 32 two-bit lanes, lane k = (s(r, 2k) + s(r, 2k+1)) mod 4
-  uint64_t v = 0;
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    uint32_t t = sw[i] & 0x03030303u;
-    uint32_t u = t + (t >> 8);                             // byte0: c0+c1, byte2: c2+c3
-    uint32_t f = (u & 3u) | (((u >> 16) & 3u) << 2);
-    v |= (uint64_t)f << (4 * i);
-  }
-  __syncthreads();   // sub[] cleared
+  // Levels below lmin are never rotated, so the sums start at level Ls = min(max(lmin,1), 4)
+  // (LMR's default lmin is 4).  Row partial at level Ls: lane k (2 bits, bits 2k..2k+1) =
+  // sum over the row's columns [k 2^Ls, (k+1) 2^Ls) of s mod 4.
   const int lmin = d.lmin;
+  const int Ls = lmin < 1 ? 1 : (lmin > 4 ? 4 : lmin);
+  uint64_t v = 0;
+  if (Ls == 1) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      uint32_t t = sw[i] & 0x03030303u;
+      uint32_t u = t + (t >> 8);                           // byte0: c0+c1, byte2: c2+c3
+      uint32_t f = (u & 3u) | (((u >> 16) & 3u) << 2);
+      v |= (uint64_t)f << (4 * i);
+    }
+  } else {
+    const int sh = Ls - 2;                                 // 2^sh words per lane
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      acc += sw[i] & 0x03030303u;                          // byte lanes, <= 12 each
+      if (((i + 1) & ((1 << sh) - 1)) == 0) {
+        const uint32_t lanev = ((acc * 0x01010101u) >> 24) & 3u;   // sum of the 4 bytes, mod 4
+        v |= (uint64_t)lanev << (2 * (i >> sh));
+        acc = 0;
+      }
+    }
+  }
+  for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
+  __syncthreads();   // sub[] cleared
   const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
   const int cov_cols = W - x0;
-  for (int L = 1; L <= 6; L++) {
-    if (L > 1) v = pair4(v);                               // widen the columns
+  for (int L = Ls; L <= 6; L++) {
+    if (L > Ls) v = pair4(v);                              // widen the columns
     if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
     else {
       if (lane == 0) l6_part[warp] = v;
