@@ -167,6 +167,126 @@ const char *rdhei_stage_name(int op, int stage);
 int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Security and quality statistics (Sec. IV-C, Tab. analysis; PSNR and SSIM of the
+ * reconstructed image, Sec. IV) for a batch of 8-bit images:
+ *   entropy  H(a) = -sum_v P(v) log2 P(v), P = grey-level histogram of a / (H W),
+ *            with 0 log2 0 = 0;
+ *   chi2     256 (H W) sum_v (P(v) - 1/256)^2 -- the printed formula, i.e. Pearson's
+ *            statistic against equal counts (about 255 for a uniform image; the
+ *            paper's table lists values near its square root);
+ * and, when b is given (same size):
+ *   NPCR     100 * #{pixels with a != b} / (H W).  The printed indicator reads
+ *            "equal", which the paper's own table values (about 99.6 % between an
+ *            image and its encryption) rule out;
+ *   UACI     100 * sum |a - b| / (255 H W);
+ *   PSNR     10 log10(255^2 / MSE), MSE = sum (a - b)^2 / (H W); +inf when a == b;
+ *   SSIM     only with RDHEI_STATS_SSIM: Wang et al. 2004 with an 11 x 11 Gaussian
+ *            window (sigma 1.5, weights summing to 1), C1 = (0.01 * 255)^2,
+ *            C2 = (0.03 * 255)^2, averaged over every window position inside the
+ *            image; NaN when H or W is below 11 or the flag is not set.  The paper
+ *            reports SSIM without defining it; this is the standard definition.
+ * Without b, n_diff / sum_abs / sum_sq are 0 and npcr, uaci, psnr, ssim are NaN.
+ * Exact integers: hist, n_diff, sum_abs, sum_sq.  entropy, chi2, npcr, uaci and psnr
+ * are fp64 functions of them.  SSIM's local moments are fp32 (pixels centred at 128),
+ * the window average fp64; its error against an fp64 evaluation is below 1e-4.
+ *
+ * Ownership: a, b and out are device memory owned by the caller; out must be 8-byte
+ * aligned.  The workspace (256-byte aligned device memory of at least
+ * rdhei_stats_workspace_size bytes) is scratch for the call.  The call copies its
+ * descriptors to the workspace and waits for that copy, then launches two kernels
+ * without waiting.  Errors: RDHEI_EINVAL (bad sizes, H * W > 2^31, null or misaligned
+ * pointers), RDHEI_ESPACE (workspace too small), RDHEI_ECUDA. */
+#define RDHEI_STATS_SSIM 1u
+
+typedef struct rdhei_stats {
+    uint32_t hist[256];
+    uint64_t n_diff;      /* pixels where a != b */
+    uint64_t sum_abs;     /* sum |a - b| */
+    uint64_t sum_sq;      /* sum (a - b)^2 */
+    double entropy, chi2, npcr, uaci, psnr, ssim;
+} rdhei_stats;
+
+typedef struct rdhei_stats_job {
+    int32_t H, W;
+    uint32_t flags;       /* RDHEI_STATS_SSIM or 0 */
+    uint32_t reserved;
+    const uint8_t *a;     /* device image, row-major H x W */
+    const uint8_t *b;     /* device image compared with a, or NULL */
+    rdhei_stats *out;     /* device */
+} rdhei_stats_job;
+
+size_t rdhei_stats_workspace_size(const rdhei_stats_job *jobs, int n);
+int rdhei_image_stats(const rdhei_stats_job *jobs, int n, void *ws, size_t ws_bytes, void *stream);
+
+/* The same call split for repeated use: create validates the jobs and uploads their
+ * descriptors into the workspace (host-synchronous, like rdhei_plan_upload); run
+ * issues one memset and the kernels only (capturable into a CUDA graph), writing
+ * every job's out again; stage 0 is the histogram / pair-sum pass, stage 1 the SSIM
+ * stencil.  The workspace and the images must stay valid while the plan is used;
+ * destroy frees the host-side object only. */
+typedef struct rdhei_stats_plan rdhei_stats_plan;
+int rdhei_stats_plan_create(const rdhei_stats_job *jobs, int n, void *ws, size_t ws_bytes, void *stream,
+                            rdhei_stats_plan **plan);
+int rdhei_stats_plan_run(rdhei_stats_plan *plan, void *stream);
+int rdhei_stats_plan_run_stage(rdhei_stats_plan *plan, int stage, void *stream);
+void rdhei_stats_plan_destroy(rdhei_stats_plan *plan);
+
+/* ---------------------------------------------------------------------------------
+ * LMR side information (Sec. III-B-1, "Maps generation, rotation, and compression"
+ * and "Maps embedding"; Sec. III-B-2/3, the hider and receiver read it back).  The
+ * paper compresses rot(eta) and rot(l) with JBIG-KIT and writes the concatenation
+ * into the first MSB plane; when it does not fit into H * W bits the owner moves to
+ * the next most optimal b.  These HOST functions are a JBIG-style replacement of this
+ * project's design:
+ *   context   10 causal neighbours: row y-2 at x-1, x, x+1; row y-1 at x-2 .. x+2;
+ *             row y at x-2, x-1 (most significant context bit first); outside = 0;
+ *   model     per context counts c0 = c1 = 1 at the start, +2 per coded symbol;
+ *             when c0 + c1 > 8192 both become (c >> 1) | 1;
+ *   coder     binary arithmetic coding (Witten, Neal, Cleary 1987), 32-bit low/high,
+ *             symbol 0 = the lower floor(range * c0 / (c0 + c1)) values, two
+ *             terminating bits, MSB-first bytes zero-padded.
+ * Container (the first side_nbits bits of the first MSB plane, i.e. bit 7 of pixels
+ * 0 .. side_nbits - 1 of the rotated image): byte 0 = b; bytes 1..4, 5..8 = byte
+ * lengths of the rot(eta) and rot(l) streams, big-endian; then both streams.
+ *
+ * All buffers here are HOST memory; bitmaps are H * W bits in the stream convention.
+ * rdhei_lmr_side_pack: per job, compress eta_bits and map_bits (for the job's b) into
+ *   side (capacity floor(H * W / 8) bytes); status RDHEI_ECAPACITY when the container
+ *   does not fit (the caller tries its next b), RDHEI_EINVAL for bad arguments.
+ * rdhei_lmr_side_unpack: per job, read b and both maps from a first-MSB plane
+ *   (plane: ceil(H * W / 8) bytes); status RDHEI_EINVAL for a malformed container.
+ * Both spread the jobs over `threads` host threads (0 = all cores) and return
+ * RDHEI_EINVAL only for a bad job array; per-job results are in status.
+ * rdhei_msb_plane (DEVICE, asynchronous on stream): bit 7 of every pixel of a device
+ *   image, packed into out_bits (4-byte aligned, ceil(H * W / 32) words). */
+typedef struct rdhei_side_pack_job {
+    int32_t H, W;
+    int32_t b;                /* in: the b whose location map is map_bits (2..8) */
+    int32_t status;           /* out */
+    const uint8_t *eta_bits;  /* in: rot(eta), H * W bits */
+    const uint8_t *map_bits;  /* in: rot(l_b), H * W bits */
+    uint8_t *side;            /* out: container, floor(H * W / 8) bytes available */
+    uint64_t side_nbits;      /* out: container length in bits (0 on failure) */
+} rdhei_side_pack_job;
+
+typedef struct rdhei_side_unpack_job {
+    int32_t H, W;
+    int32_t b;                /* out */
+    int32_t status;           /* out */
+    const uint8_t *plane;     /* in: first MSB plane, ceil(H * W / 8) bytes */
+    uint8_t *eta_bits;        /* out: rot(eta), ceil(H * W / 8) bytes */
+    uint8_t *map_bits;        /* out: rot(l_b), ceil(H * W / 8) bytes */
+} rdhei_side_unpack_job;
+
+int rdhei_bilevel_encode(const uint8_t *bits, int H, int W, uint8_t *out, size_t cap, size_t *len);
+int rdhei_bilevel_decode(const uint8_t *in, size_t len, int H, int W, uint8_t *bits);
+int rdhei_lmr_side_pack(rdhei_side_pack_job *jobs, int n, int threads);
+int rdhei_lmr_side_unpack(rdhei_side_unpack_job *jobs, int n, int threads);
+int rdhei_msb_plane(const uint8_t *src, int H, int W, uint8_t *out_bits, void *stream);
+size_t rdhei_side_pack_job_size(void);
+size_t rdhei_side_unpack_job_size(void);
+
+/* ---------------------------------------------------------------------------------
  * Extraction without any allocation.  The paper has no counterpart to this call; it
  * exists for callers that cannot allocate device memory at all -- code that runs in a
  * host callback or under a runtime that owns every allocation, or a tool that links
@@ -194,6 +314,8 @@ int rdhei_workspace_status(void *ws, void *stream, int32_t *code);
 /* sizeof(rdhei_job) and sizeof(rdhei_info), for bindings that build them by hand. */
 size_t rdhei_job_size(void);
 size_t rdhei_info_size(void);
+size_t rdhei_stats_size(void);
+size_t rdhei_stats_job_size(void);
 
 /* Library version and build target, e.g. "rdhei 0.1 sm_103a". */
 const char *rdhei_version(void);

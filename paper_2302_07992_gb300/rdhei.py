@@ -18,6 +18,7 @@ from . import build as _build
 EMR, LMR = 0, 1
 OP_LABEL_ENCRYPT, OP_EMBED, OP_EXTRACT, OP_DECRYPT_RECOVER, OP_LMR_SET_SIDE = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE"}
+RDHEI_OK, RDHEI_EINVAL, RDHEI_ECAPACITY, RDHEI_ECUDA, RDHEI_ETIMEOUT, RDHEI_ESPACE = range(6)
 
 if not os.path.exists(_build.LIB):
     raise ImportError(f"{_build.LIB} is missing: build it with `python -m paper_2302_07992_gb300.build` "
@@ -303,3 +304,226 @@ def extract_noalloc_job(job: Job, stream=None) -> int:
     callers that cannot allocate device memory: the library uses a static device
     array instead of a workspace (one image, at most NOALLOC_MAX_PIXELS pixels)."""
     return int(_lib.rdhei_extract_noalloc(ctypes.byref(job), _stream(stream)))
+
+
+# ------------------------------------------------------ security statistics --
+STATS_SSIM = 1
+
+
+class StatsJob(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("hist", ctypes.c_uint32 * 256), ("n_diff", ctypes.c_uint64), ("sum_abs", ctypes.c_uint64),
+                ("sum_sq", ctypes.c_uint64), ("entropy", ctypes.c_double), ("chi2", ctypes.c_double),
+                ("npcr", ctypes.c_double), ("uaci", ctypes.c_double), ("psnr", ctypes.c_double),
+                ("ssim", ctypes.c_double)]
+
+
+STATS_BYTES = ctypes.sizeof(Stats)
+_StatsJobP = ctypes.POINTER(StatsJob)
+_lib.rdhei_stats_workspace_size.argtypes = [_StatsJobP, ctypes.c_int]
+_lib.rdhei_stats_workspace_size.restype = ctypes.c_size_t
+_lib.rdhei_image_stats.argtypes = [_StatsJobP, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+_lib.rdhei_image_stats.restype = ctypes.c_int
+_lib.rdhei_stats_size.restype = ctypes.c_size_t
+_lib.rdhei_stats_job_size.restype = ctypes.c_size_t
+assert _lib.rdhei_stats_size() == STATS_BYTES, "rdhei_stats layout mismatch"
+assert _lib.rdhei_stats_job_size() == ctypes.sizeof(StatsJob), "rdhei_stats_job layout mismatch"
+
+
+def stats_job(a: torch.Tensor, b: torch.Tensor | None, out: torch.Tensor, ssim: bool = False) -> StatsJob:
+    """Job for one image (and its comparison image b); ``out`` is STATS_BYTES of device memory."""
+    H, W = a.shape
+    if b is not None:
+        assert tuple(b.shape) == (H, W)
+    j = StatsJob()
+    j.H, j.W, j.flags = int(H), int(W), STATS_SSIM if ssim else 0
+    j.a, j.b, j.out = _ptr(a), _ptr(b), _ptr(out)
+    return j
+
+
+def new_stats(n: int = 1, device="cuda") -> torch.Tensor:
+    return torch.zeros((n, STATS_BYTES), dtype=torch.uint8, device=device)
+
+
+def read_stats(out: torch.Tensor) -> list[dict]:
+    host = out.detach().to("cpu").contiguous()
+    res = []
+    for i in range(host.shape[0]):
+        s = Stats.from_buffer_copy(bytes(host[i].numpy().tobytes()))
+        res.append({"hist": list(s.hist), "n_diff": s.n_diff, "sum_abs": s.sum_abs, "sum_sq": s.sum_sq,
+                    "entropy": s.entropy, "chi2": s.chi2, "npcr": s.npcr, "uaci": s.uaci, "psnr": s.psnr,
+                    "ssim": s.ssim})
+    return res
+
+
+_lib.rdhei_stats_plan_create.argtypes = [_StatsJobP, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+_lib.rdhei_stats_plan_create.restype = ctypes.c_int
+_lib.rdhei_stats_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+_lib.rdhei_stats_plan_run.restype = ctypes.c_int
+_lib.rdhei_stats_plan_run_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+_lib.rdhei_stats_plan_run_stage.restype = ctypes.c_int
+_lib.rdhei_stats_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.rdhei_stats_plan_destroy.restype = None
+STATS_STAGES = ("stats_hist_pairs", "stats_ssim")
+
+
+class StatsCall:
+    """A stats plan: jobs validated and uploaded once (host-synchronous); ``run``
+    launches the memset and kernels only, so it can be timed per stage or captured."""
+
+    def __init__(self, jobs: list[StatsJob], stream=None):
+        self._jobs = (StatsJob * len(jobs))(*jobs)
+        self.n = len(jobs)
+        need = _lib.rdhei_stats_workspace_size(self._jobs, self.n)
+        if self.n and need == 0:
+            raise RdheiError("rdhei_stats_workspace_size rejected the jobs")
+        self._ws = torch.empty(int(need) + 256, dtype=torch.uint8, device="cuda")
+        off = (-self._ws.data_ptr()) % 256
+        h = ctypes.c_void_p()
+        _check(_lib.rdhei_stats_plan_create(self._jobs, self.n, ctypes.c_void_p(self._ws.data_ptr() + off),
+                                            self._ws.numel() - off, _stream(stream), ctypes.byref(h)),
+               "rdhei_stats_plan_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.rdhei_stats_plan_run(self._h, _stream(stream)), "rdhei_stats_plan_run")
+
+    def run_stage(self, stage: int, stream=None):
+        _check(_lib.rdhei_stats_plan_run_stage(self._h, int(stage), _stream(stream)), "rdhei_stats_plan_run_stage")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.rdhei_stats_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def image_stats_once(jobs: list[StatsJob], stream=None):
+    """rdhei_image_stats: validate, upload and launch in one call (workspace freed after)."""
+    arr = (StatsJob * len(jobs))(*jobs)
+    need = _lib.rdhei_stats_workspace_size(arr, len(jobs))
+    if jobs and need == 0:
+        raise RdheiError("rdhei_stats_workspace_size rejected the jobs")
+    ws = torch.empty(int(need) + 256, dtype=torch.uint8, device="cuda")
+    off = (-ws.data_ptr()) % 256
+    _check(_lib.rdhei_image_stats(arr, len(jobs), ctypes.c_void_p(ws.data_ptr() + off), ws.numel() - off,
+                                  _stream(stream)), "rdhei_image_stats")
+
+
+def image_stats(pairs, ssim: bool = False, stream=None) -> list[dict]:
+    """Statistics of each (a, b) pair of device uint8 images (b may be None), in one call."""
+    out = new_stats(len(pairs))
+    call = StatsCall([stats_job(a, b, out[i], ssim) for i, (a, b) in enumerate(pairs)])
+    call.run(stream)
+    return read_stats(out)
+
+
+# ------------------------------------------------- LMR side information (host) --
+class SidePackJob(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("b", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("eta_bits", ctypes.c_void_p), ("map_bits", ctypes.c_void_p), ("side", ctypes.c_void_p),
+                ("side_nbits", ctypes.c_uint64)]
+
+
+class SideUnpackJob(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("b", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("plane", ctypes.c_void_p), ("eta_bits", ctypes.c_void_p), ("map_bits", ctypes.c_void_p)]
+
+
+_lib.rdhei_bilevel_encode.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+_lib.rdhei_bilevel_encode.restype = ctypes.c_int
+_lib.rdhei_bilevel_decode.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+_lib.rdhei_bilevel_decode.restype = ctypes.c_int
+_lib.rdhei_lmr_side_pack.argtypes = [ctypes.POINTER(SidePackJob), ctypes.c_int, ctypes.c_int]
+_lib.rdhei_lmr_side_pack.restype = ctypes.c_int
+_lib.rdhei_lmr_side_unpack.argtypes = [ctypes.POINTER(SideUnpackJob), ctypes.c_int, ctypes.c_int]
+_lib.rdhei_lmr_side_unpack.restype = ctypes.c_int
+_lib.rdhei_msb_plane.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rdhei_msb_plane.restype = ctypes.c_int
+_lib.rdhei_side_pack_job_size.restype = ctypes.c_size_t
+_lib.rdhei_side_unpack_job_size.restype = ctypes.c_size_t
+assert _lib.rdhei_side_pack_job_size() == ctypes.sizeof(SidePackJob), "rdhei_side_pack_job layout mismatch"
+assert _lib.rdhei_side_unpack_job_size() == ctypes.sizeof(SideUnpackJob), "rdhei_side_unpack_job layout mismatch"
+
+
+def _host_u8(a, nbytes=None):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint8).reshape(-1))
+    if nbytes is not None and a.size < nbytes:
+        a = np.concatenate([a, np.zeros(nbytes - a.size, np.uint8)])
+    return a
+
+
+def bilevel_encode(bits, H: int, W: int) -> bytes:
+    """Compress H * W packed bits (host) with the library's bi-level coder."""
+    import numpy as np
+    src = _host_u8(bits, (H * W + 7) // 8)
+    cap = (H * W) // 4 + 64
+    out = np.zeros(cap, np.uint8)
+    n = ctypes.c_size_t(0)
+    _check(_lib.rdhei_bilevel_encode(src.ctypes.data, H, W, out.ctypes.data, cap, ctypes.byref(n)),
+           "rdhei_bilevel_encode")
+    return out[: n.value].tobytes()
+
+
+def bilevel_decode(data: bytes, H: int, W: int):
+    import numpy as np
+    src = np.frombuffer(bytes(data), np.uint8)
+    out = np.zeros((H * W + 7) // 8, np.uint8)
+    _check(_lib.rdhei_bilevel_decode(src.ctypes.data if src.size else None, src.size, H, W, out.ctypes.data),
+           "rdhei_bilevel_decode")
+    return out
+
+
+def lmr_side_pack(items, threads: int = 0) -> list[dict]:
+    """items: (eta_bits, map_bits, H, W, b) with host packed maps.  Per item: status,
+    the container bytes and its bit length (RDHEI_ECAPACITY when it does not fit)."""
+    import numpy as np
+    keep, jobs = [], (SidePackJob * len(items))()
+    for i, (eta, lm, H, W, b) in enumerate(items):
+        nb = (H * W + 7) // 8
+        e, m, s = _host_u8(eta, nb), _host_u8(lm, nb), np.zeros(max((H * W) // 8, 1), np.uint8)
+        keep.append((e, m, s))
+        jobs[i].H, jobs[i].W, jobs[i].b = H, W, b
+        jobs[i].eta_bits, jobs[i].map_bits, jobs[i].side = e.ctypes.data, m.ctypes.data, s.ctypes.data
+    _check(_lib.rdhei_lmr_side_pack(jobs, len(items), threads), "rdhei_lmr_side_pack")
+    out = []
+    for i in range(len(items)):
+        nbits = int(jobs[i].side_nbits)
+        out.append({"status": int(jobs[i].status), "side_nbits": nbits, "side": keep[i][2][: nbits // 8].copy()})
+    return out
+
+
+def lmr_side_unpack(items, threads: int = 0) -> list[dict]:
+    """items: (plane, H, W) with the host first-MSB plane.  Per item: status, b and the
+    packed rot(eta), rot(l)."""
+    import numpy as np
+    keep, jobs = [], (SideUnpackJob * len(items))()
+    for i, (plane, H, W) in enumerate(items):
+        nb = (H * W + 7) // 8
+        p, e, m = _host_u8(plane, nb), np.zeros(nb, np.uint8), np.zeros(nb, np.uint8)
+        keep.append((p, e, m))
+        jobs[i].H, jobs[i].W = H, W
+        jobs[i].plane, jobs[i].eta_bits, jobs[i].map_bits = p.ctypes.data, e.ctypes.data, m.ctypes.data
+    _check(_lib.rdhei_lmr_side_unpack(jobs, len(items), threads), "rdhei_lmr_side_unpack")
+    return [{"status": int(jobs[i].status), "b": int(jobs[i].b), "eta_bits": keep[i][1], "map_bits": keep[i][2]}
+            for i in range(len(items))]
+
+
+def msb_plane(img: torch.Tensor, stream=None) -> torch.Tensor:
+    """Bit 7 of every pixel of a device image, packed (device, word-padded)."""
+    H, W = img.shape
+    out = bitbuf(H * W, img.device)
+    _check(_lib.rdhei_msb_plane(_ptr(img), H, W, _ptr(out), _stream(stream)), "rdhei_msb_plane")
+    return out
