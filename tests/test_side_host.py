@@ -1,0 +1,110 @@
+"""The library's host side-information coder (rdhei_bilevel_*, rdhei_lmr_side_*) against
+the oracle coder, bit for bit.  Host functions only: runs without a GPU."""
+import numpy as np
+import pytest
+
+from oracle import sidecoder as sc
+from paper_2302_07992_gb300 import synth
+
+
+def _rd():
+    from paper_2302_07992_gb300 import build
+    build.build()                      # host functions of the library; nothing is launched
+    from paper_2302_07992_gb300 import rdhei
+    return rdhei
+
+
+def _bitmap(kind, H, W, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "random":
+        return rng.integers(0, 2, (H, W)).astype(np.uint8)
+    if kind == "sparse":
+        return (rng.random((H, W)) < 0.03).astype(np.uint8)
+    if kind == "dense":
+        return (rng.random((H, W)) < 0.9).astype(np.uint8)
+    if kind == "labels":                      # a location map of a synthetic image (left-neighbour test)
+        img = synth.synth_image(H, W, seed, noise_sigma=3.0)
+        left = np.concatenate([np.zeros((H, 1), np.int64), img[:, :-1].astype(np.int64)], axis=1)
+        return (((img.astype(np.int64) ^ left) >> 4) != 0).astype(np.uint8)
+    return np.zeros((H, W), np.uint8)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (5, 3), (33, 65), (64, 64), (96, 130)])
+@pytest.mark.parametrize("kind", ["random", "sparse", "dense", "labels", "zeros"])
+def test_bilevel_matches_oracle(shape, kind):
+    rd = _rd()
+    H, W = shape
+    bm = _bitmap(kind, H, W, H * 1000 + W)
+    packed = np.packbits(bm.reshape(-1))
+    lib = rd.bilevel_encode(packed, H, W)
+    assert lib == sc.encode_bitmap(bm)
+    back = rd.bilevel_decode(lib, H, W)
+    assert np.array_equal(np.unpackbits(back)[: H * W].reshape(H, W), bm)
+
+
+def test_pack_unpack_match_oracle_container():
+    rd = _rd()
+    items, want = [], []
+    for i, (H, W) in enumerate([(48, 64), (64, 48), (90, 33), (128, 128)]):
+        eta = _bitmap("labels", H, W, 10 + i)
+        lm = _bitmap("labels", H, W, 20 + i)
+        b = 2 + i
+        items.append((np.packbits(eta.reshape(-1)), np.packbits(lm.reshape(-1)), H, W, b))
+        want.append(sc.pack_side(eta, lm, b))
+    got = rd.lmr_side_pack(items, threads=3)
+    for g, w, it in zip(got, want, items):
+        H, W = it[2], it[3]
+        fits = 8 * len(w) <= H * W
+        if fits:
+            assert g["status"] == rd.RDHEI_OK and g["side"].tobytes() == w and g["side_nbits"] == 8 * len(w)
+        else:
+            assert g["status"] == rd.RDHEI_ECAPACITY and g["side_nbits"] == 0
+    # unpack from a plane that carries the container followed by other bits
+    planes = []
+    for g, it in zip(got, items):
+        H, W = it[2], it[3]
+        plane = np.random.default_rng(H).integers(0, 256, (H * W + 7) // 8).astype(np.uint8)
+        if g["status"] == rd.RDHEI_OK:
+            plane[: len(g["side"])] = g["side"]
+        planes.append((plane, H, W))
+    back = rd.lmr_side_unpack(planes, threads=2)
+    for r, g, it in zip(back, got, items):
+        if g["status"] != rd.RDHEI_OK:
+            continue
+        assert r["status"] == rd.RDHEI_OK and r["b"] == it[4]
+        n = (it[2] * it[3] + 7) // 8
+        assert np.array_equal(r["eta_bits"][:n], it[0]) and np.array_equal(r["map_bits"][:n], it[1])
+
+
+def test_incompressible_maps_do_not_fit():
+    rd = _rd()
+    H, W = 64, 64
+    noise = np.packbits(_bitmap("random", H, W, 1).reshape(-1))
+    r = rd.lmr_side_pack([(noise, noise, H, W, 3)])[0]
+    assert r["status"] == rd.RDHEI_ECAPACITY and r["side_nbits"] == 0
+
+
+def test_malformed_containers_are_rejected():
+    rd = _rd()
+    H, W = 32, 32
+    bad_b = np.zeros(128, np.uint8)
+    bad_b[0] = 9
+    too_long = np.zeros(128, np.uint8)
+    too_long[0] = 3
+    too_long[1:5] = [0, 0, 1, 0]              # 256 bytes > the 128-byte plane
+    res = rd.lmr_side_unpack([(bad_b, H, W), (too_long, H, W), (np.zeros(1, np.uint8), 2, 2)])
+    assert [r["status"] for r in res] == [rd.RDHEI_EINVAL] * 3
+
+
+def test_many_jobs_on_a_thread_pool_match_one_by_one():
+    rd = _rd()
+    items = []
+    for i in range(40):
+        H, W = 16 + i, 70 - i
+        items.append((np.packbits(_bitmap("sparse", H, W, i).reshape(-1)),
+                      np.packbits(_bitmap("labels", H, W, i).reshape(-1)), H, W, 4))
+    pooled = rd.lmr_side_pack(items, threads=8)
+    single = [rd.lmr_side_pack([it], threads=1)[0] for it in items]
+    for a, b in zip(pooled, single):
+        assert a["status"] == b["status"] and a["side_nbits"] == b["side_nbits"]
+        assert a["side"].tobytes() == b["side"].tobytes()
