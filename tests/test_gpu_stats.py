@@ -95,7 +95,7 @@ def test_constant_images():
     got = rd.image_stats([(_dev(a), _dev(a))], ssim=True)[0]
     assert got["hist"][7] == 70 * 90 and got["entropy"] == 0.0
     assert abs(got["chi2"] - 255.0 * 70 * 90) < 1e-6
-    assert got["psnr"] == math.inf and got["npcr"] == 0.0 and abs(got["ssim"] - 1.0) < 1e-6
+    assert got["psnr"] == math.inf and got["npcr"] == 0.0 and abs(got["ssim"] - 1.0) < SSIM_TOL
 
 
 def test_batch_of_uneven_pairs_in_one_call():
