@@ -15,6 +15,8 @@ from dataclasses import dataclass
 import numpy as np
 
 EMR, LMR = 0, 1
+# EMR / LMR with the MED predictor of the related work (Sec. II) instead of the glide
+EMR_MED, LMR_MED = 2, 3
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rdhei_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
@@ -52,6 +54,8 @@ def _declare(L):
     L.orc_chacha20_block.argtypes = [_u8p, c.c_uint32, _u8p, _u8p]
     L.orc_glide_labels.argtypes = [_u8p, c.c_int, c.c_int, c.c_int, _u8p]
     L.orc_label_hist.argtypes = [_u8p, c.c_int, c.c_int, _u32p]
+    L.orc_med_labels.argtypes = [_u8p, c.c_int, c.c_int, c.c_int, c.c_int, _u8p]
+    L.orc_med_hist.argtypes = [_u8p, c.c_int, c.c_int, c.c_int, _u32p]
     L.orc_choose_b.argtypes = [c.c_int, _u32p]
     L.orc_choose_b.restype = c.c_int
     L.orc_levels.argtypes = [c.c_int, c.c_int]
@@ -123,6 +127,24 @@ def label_hist(img: np.ndarray) -> np.ndarray:
     H, W = img.shape
     h = np.zeros(9, np.uint32)
     lib().orc_label_hist(_p(img), H, W, h.ctypes.data_as(_u32p))
+    return h
+
+
+def med_labels(img: np.ndarray, b: int, seven: bool) -> np.ndarray:
+    """b-MSB location map against the MED prediction (related work, Sec. II);
+    seven: predict on the top seven bits (EMR layout)."""
+    img = np.ascontiguousarray(img, np.uint8)
+    H, W = img.shape
+    out = np.zeros((H, W), np.uint8)
+    lib().orc_med_labels(_p(img), H, W, int(bool(seven)), int(b), _p(out))
+    return out
+
+
+def med_hist(img: np.ndarray, seven: bool) -> np.ndarray:
+    img = np.ascontiguousarray(img, np.uint8)
+    H, W = img.shape
+    h = np.zeros(9, np.uint32)
+    lib().orc_med_hist(_p(img), H, W, int(bool(seven)), h.ctypes.data_as(_u32p))
     return h
 
 

@@ -37,6 +37,11 @@
 
 #define ORC_EMR 0
 #define ORC_LMR 1
+/* Variants 2 and 3 are EMR and LMR with the MED predictor of the paper's related
+ * work (Sec. II) in place of the glide; bit 1 of the variant selects the predictor,
+ * bit 0 the EMR / LMR layout. */
+#define ORC_MED 2
+#define ORC_BASE(v) ((v) & 1)
 
 /* ------------------------------------------------------------------------ */
 /* ChaCha20 block function, written from RFC 8439 Sec. 2.1-2.3.             */
@@ -177,7 +182,9 @@ void orc_label_hist(const uint8_t *I, int H, int W, uint32_t hist[9])
  * Ties go to the smallest b (the paper does not say). */
 int orc_choose_b(int variant, const uint32_t hist[9])
 {
-    int b, best_b = 2, hi = variant == ORC_EMR ? 7 : 8;
+    int b, best_b = 2, hi;
+    variant = ORC_BASE(variant);
+    hi = variant == ORC_EMR ? 7 : 8;
     uint64_t best = 0;
     for (b = 2; b <= hi; b++) {
         uint64_t zeros = 0, cap;
@@ -187,6 +194,77 @@ int orc_choose_b(int variant, const uint32_t hist[9])
         if (b == 2 || cap > best) { best = cap; best_b = b; }
     }
     return best_b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Related-work predictor (not the paper's method): the median edge detector  */
+/* (MED, the LOCO-I predictor) that Sec. II quotes for Puyang et al.'s two-MSB  */
+/* prediction and Puteaux et al.'s recursive labelling.  With A the left, B the */
+/* upper and C the upper-left neighbour:                                       */
+/*   pred = min(A, B) if C >= max(A, B); max(A, B) if C <= min(A, B);          */
+/*   pred = A + B - C otherwise.                                               */
+/* (The first printed form compares C with min(A, B) in its second case; the   */
+/* LOCO-I form quoted second, used here, compares with max in the first.)      */
+/* Borders: pixel (0, 0) has no prediction; row 0 predicts from the left       */
+/* neighbour, column 0 from the upper one.  EMR loses the LSB plane at the     */
+/* receiver, so its prediction works on the top seven bits (v >> 1) and is     */
+/* shifted back; LMR recovers exactly and predicts on all eight bits.          */
+/* ------------------------------------------------------------------------ */
+static int orc_med(int A, int B, int C)
+{
+    int mx = A > B ? A : B, mn = A < B ? A : B;
+    if (C >= mx) return mn;
+    if (C <= mn) return mx;
+    return A + B - C;
+}
+
+/* Prediction of pixel (i, j) from image V (original at the owner, recovered at the
+ * receiver); -1 for pixel (0, 0). */
+static int orc_med_pred(const uint8_t *V, int W, int i, int j, int seven)
+{
+    int s = seven ? 1 : 0, A, B, C;
+    if (i == 0 && j == 0) return -1;
+    if (i == 0) return (V[j - 1] >> s) << s;
+    if (j == 0) return (V[(size_t)(i - 1) * W] >> s) << s;
+    A = V[(size_t)i * W + j - 1] >> s;
+    B = V[(size_t)(i - 1) * W + j] >> s;
+    C = V[(size_t)(i - 1) * W + j - 1] >> s;
+    return orc_med(A, B, C) << s;
+}
+
+/* Multi-MSB label against the MED prediction: t = number of leading bits (of 8)
+ * in which the pixel equals its prediction, 0 for pixel (0, 0).  The b-MSB map is
+ * l = 1 where t < b. */
+static void orc_med_t(const uint8_t *I, int H, int W, int seven, uint8_t *T)
+{
+    int i, j, k;
+    for (i = 0; i < H; i++)
+        for (j = 0; j < W; j++) {
+            int pr = orc_med_pred(I, W, i, j, seven), x = I[(size_t)i * W + j], t = 0;
+            if (pr >= 0)
+                for (k = 7; k >= 0 && ((x >> k) & 1) == ((pr >> k) & 1); k--) t++;
+            T[(size_t)i * W + j] = (uint8_t)t;
+        }
+}
+
+void orc_med_labels(const uint8_t *I, int H, int W, int seven, int b, uint8_t *L)
+{
+    size_t n = (size_t)H * W, p;
+    uint8_t *T = (uint8_t *)malloc(n ? n : 1);
+    orc_med_t(I, H, W, seven, T);
+    for (p = 0; p < n; p++) L[p] = T[p] < b;
+    free(T);
+}
+
+void orc_med_hist(const uint8_t *I, int H, int W, int seven, uint32_t hist[9])
+{
+    size_t n = (size_t)H * W, p;
+    uint8_t *T = (uint8_t *)malloc(n ? n : 1);
+    int k;
+    orc_med_t(I, H, W, seven, T);
+    for (k = 0; k < 9; k++) hist[k] = 0;
+    for (p = 0; p < n; p++) hist[T[p]]++;
+    free(T);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -268,7 +346,7 @@ void orc_rotate(uint8_t **planes, int nplanes, int H, int W, const uint8_t *s, i
 int orc_effective_lmin(int variant, int lmin, int H, int W)
 {
     int n = orc_levels(H, W);
-    if (lmin <= 0) lmin = variant == ORC_EMR ? 1 : 4;
+    if (lmin <= 0) lmin = ORC_BASE(variant) == ORC_EMR ? 1 : 4;
     if (n >= 1 && lmin > n) lmin = n;
     return lmin;
 }
@@ -292,11 +370,13 @@ int orc_label_encrypt(int variant, int b_req, int lmin, int rot_enable,
     size_t n = (size_t)H * W, p;
     uint8_t *L, *eta, *rotI, *s;
     uint8_t *planes[3];
-    int b, t;
+    int b, t, med = variant & ORC_MED;
     uint64_t zeros = 0;
 
+    variant = ORC_BASE(variant);
     /* location map generation and choice of b */
-    orc_label_hist(I, H, W, hist);
+    if (med) orc_med_hist(I, H, W, variant == ORC_EMR, hist);
+    else orc_label_hist(I, H, W, hist);
     b = b_req > 0 ? b_req : orc_choose_b(variant, hist);
     for (t = b; t <= 8; t++) zeros += hist[t];
     *b_out = b;
@@ -306,7 +386,8 @@ int orc_label_encrypt(int variant, int b_req, int lmin, int rot_enable,
     eta = (uint8_t *)malloc(n ? n : 1);
     rotI = (uint8_t *)malloc(n ? n : 1);
     s = (uint8_t *)malloc(n ? n : 1);
-    orc_glide_labels(I, H, W, b, L);
+    if (med) orc_med_labels(I, H, W, variant == ORC_EMR, b, L);
+    else orc_glide_labels(I, H, W, b, L);
 
     /* first MSB map, Eq. (MSB_map): eta = (I AND 128) mod 127 */
     for (p = 0; p < n; p++) eta[p] = (uint8_t)((I[p] & 128) % 127);
@@ -360,7 +441,7 @@ void orc_lmr_set_side(uint8_t *enc, uint64_t npx, const uint8_t *side_bits, uint
  * plane, LMR from the (decompressed) rotated location map. */
 static int orc_hider_label(int variant, const uint8_t *img, const uint8_t *lmr_map, uint64_t q)
 {
-    return variant == ORC_EMR ? (img[q] & 1) : orc_get_bit(lmr_map, q);
+    return ORC_BASE(variant) == ORC_EMR ? (img[q] & 1) : orc_get_bit(lmr_map, q);
 }
 
 /* Embed payload bits m[0..nbits) encrypted with the K2 stream z2.  Redundant
@@ -374,8 +455,8 @@ uint64_t orc_embed(int variant, int b, const uint8_t k2[32], const uint8_t nonce
                    const uint8_t *payload, uint64_t nbits, uint8_t *marked)
 {
     uint64_t n = (uint64_t)H * W, q, k = 0;
-    int slots = variant == ORC_EMR ? b : b - 1;
-    int top = variant == ORC_EMR ? 7 : 6;
+    int slots = ORC_BASE(variant) == ORC_EMR ? b : b - 1;
+    int top = ORC_BASE(variant) == ORC_EMR ? 7 : 6;
     uint8_t *z2 = (uint8_t *)malloc((size_t)((nbits + 7) / 8 + 1));
     orc_keystream(k2, nonce2, (nbits + 7) / 8, z2);
     memcpy(marked, enc, (size_t)n);
@@ -404,8 +485,8 @@ uint64_t orc_extract(int variant, int b, const uint8_t k2[32], const uint8_t non
                      uint8_t *bits_out, uint64_t max_bits)
 {
     uint64_t n = (uint64_t)H * W, q, k = 0, cap = 0;
-    int slots = variant == ORC_EMR ? b : b - 1;
-    int top = variant == ORC_EMR ? 7 : 6;
+    int slots = ORC_BASE(variant) == ORC_EMR ? b : b - 1;
+    int top = ORC_BASE(variant) == ORC_EMR ? 7 : 6;
     uint8_t *z2;
     for (q = 0; q < n; q++)
         if (orc_hider_label(variant, marked, lmr_map, q) == 0) cap += (uint64_t)slots;
@@ -444,9 +525,11 @@ void orc_decrypt_recover(int variant, int b, int lmin, int rot_enable,
     uint8_t *L = (uint8_t *)malloc(n ? n : 1);
     uint8_t *eta = (uint8_t *)malloc(n ? n : 1);
     uint8_t *planes[3];
-    int i, j, shift = 8 - b;
-    unsigned field = variant == ORC_EMR ? ((1u << b) - 1) << shift
-                                        : ((1u << (b - 1)) - 1) << shift;
+    int i, j, shift = 8 - b, med = variant & ORC_MED;
+    unsigned field;
+
+    variant = ORC_BASE(variant);
+    field = variant == ORC_EMR ? ((1u << b) - 1) << shift : ((1u << (b - 1)) - 1) << shift;
 
     orc_keystream(k1, nonce1, n, s);
     for (p = 0; p < n; p++) {
@@ -460,6 +543,20 @@ void orc_decrypt_recover(int variant, int b, int lmin, int rot_enable,
     if (variant == ORC_LMR)
         for (p = 0; p < n; p++) out[p] = (uint8_t)((out[p] & 0x7F) | (eta[p] << 7));
 
+    if (med) {
+        /* MED variant: raster order is a causal order for the left, upper and
+         * upper-left neighbours, so each prediction sees recovered pixels only */
+        for (i = 0; i < H; i++)
+            for (j = 0; j < W; j++) {
+                size_t q = (size_t)i * W + j;
+                if (!L[q]) {
+                    int pr = orc_med_pred(out, W, i, j, variant == ORC_EMR);
+                    out[q] = (uint8_t)((out[q] & ~field) | ((unsigned)pr & field));
+                }
+            }
+        free(s); free(L); free(eta);
+        return;
+    }
     for (i = 0; i < H; i++) {
         unsigned omega = out[(size_t)i * W] & field;     /* first column is non-redundant */
         for (j = 1; j < W; j++) {
