@@ -93,31 +93,33 @@ def _oracle_pipeline(args):
     kk = image_keys(k)
     p = oracle.Params(variant=variant, k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"])
     H, W = img.shape
+    lmr = (variant & 1) == oracle.LMR
     t0 = time.perf_counter()
-    sn = side_nbits(H, W) if variant == oracle.LMR else 0
+    sn = side_nbits(H, W) if lmr else 0
     side = synth.random_bits(k, sn) if sn else None
     e = oracle.label_encrypt(p, img, side, sn)
     pay = synth.payload_bits(synth.image_seed(BASE_SEED, k), e.capacity)
-    lmap = e.map_bits if variant == oracle.LMR else None
+    lmap = e.map_bits if lmr else None
     marked, _ = oracle.embed(p, e.b, e.enc, pay, e.capacity, lmap)
     oracle.extract(p, e.b, marked, e.capacity, lmap)
-    oracle.decrypt_recover(p, e.b, marked, lmap, e.eta_bits if variant == oracle.LMR else None)
+    oracle.decrypt_recover(p, e.b, marked, lmap, e.eta_bits if lmr else None)
     return H * W, time.perf_counter() - t0
 
 
-def oracle_throughput(images, first, budget_s=15.0):
+def oracle_throughput(images, first, budget_s=15.0, med=False):
     """Oracle Mpixel/s on the host cores, one image per process, on a bounded sample."""
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0))
     # calibrate on one image (after a first call that loads the library), then size
     # the sample to ~budget_s of wall time
-    _oracle_pipeline((images[0], first, 0))
-    _, t1 = _oracle_pipeline((images[0], first, 0))
+    v0 = 2 if med else 0
+    _oracle_pipeline((images[0], first, v0))
+    _, t1 = _oracle_pipeline((images[0], first, v0))
     per_core = max(1, int(budget_s / max(t1, 1e-3)))
     n = min(len(images), per_core * cores)
     n = max(n, min(len(images), cores))
-    work = [(images[i], first + i, i % 2) for i in range(n)]
+    work = [(images[i], first + i, i % 2 + v0) for i in range(n)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
@@ -125,7 +127,8 @@ def oracle_throughput(images, first, budget_s=15.0):
     wall = time.perf_counter() - t0
     px = sum(r[0] for r in res)
     return {"value": px / wall / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} of the workload's {images.shape[1]}x{images.shape[2]} images (EMR/LMR alternating), "
+            "sample": f"{n} of the workload's {images.shape[1]}x{images.shape[2]} images "
+                      f"({'EMR_MED/LMR_MED' if med else 'EMR/LMR'} alternating), "
                       f"full pipeline each, one image per process, {wall:.1f} s wall"}
 
 
@@ -184,7 +187,7 @@ def run_gpu(args, rank, world, local_rank):
     N = H * W
     first = rank_images(rank, n).start
     imgs_np = args._images
-    variants = [rd.EMR if (first + k) % 2 == 0 else rd.LMR for k in range(n)]
+    variants = [(rd.EMR if (first + k) % 2 == 0 else rd.LMR) + (2 if args.med else 0) for k in range(n)]
     params = []
     for k in range(n):
         kk = image_keys(first + k)
@@ -201,7 +204,7 @@ def run_gpu(args, rank, world, local_rank):
     sn = side_nbits(H, W)
     side_np = np.zeros((n, ((sn + 31) // 32) * 4), np.uint8)
     for k in range(n):
-        if variants[k] == rd.LMR:
+        if (variants[k] & 1) == rd.LMR:
             b = synth.random_bits(first + k, sn)
             side_np[k, :b.size] = b
     sides = torch.from_numpy(side_np).to(dev)
@@ -212,7 +215,7 @@ def run_gpu(args, rank, world, local_rank):
 
     enc_jobs = []
     for k in range(n):
-        lmr = variants[k] == rd.LMR
+        lmr = (variants[k] & 1) == rd.LMR
         enc_jobs.append(rd.make_job(params[k], H, W, src=imgs[k], dst=enc[k], map_bits=maps[k] if lmr else None,
                                     eta_bits=etas[k] if lmr else None, side_bits=sides[k] if lmr else None,
                                     side_nbits=sn if lmr else 0, info=info[k]))
@@ -230,7 +233,7 @@ def run_gpu(args, rank, world, local_rank):
 
     emb_jobs, ext_jobs, dec_jobs = [], [], []
     for k in range(n):
-        lmr = variants[k] == rd.LMR
+        lmr = (variants[k] & 1) == rd.LMR
         m = maps[k] if lmr else None
         emb_jobs.append(rd.make_job(params[k], H, W, src=enc[k], dst=marked[k], map_bits=m, payload=payload[k],
                                     nbits=caps[k], info=info[k], b=0))
@@ -241,7 +244,7 @@ def run_gpu(args, rank, world, local_rank):
     plan_emb, plan_ext, plan_dec = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream), rd.Plan(dec_jobs, stream)
     plans = [(plan_enc, rd.OP_LABEL_ENCRYPT), (plan_emb, rd.OP_EMBED), (plan_ext, rd.OP_EXTRACT),
              (plan_dec, rd.OP_DECRYPT_RECOVER)]
-    stage_list = [(pl, op, s, f"{rd.stages(op)[s]}") for pl, op in plans for s in range(len(rd.stages(op)))]
+    stage_list = [(pl, op, s, f"{rd.stages(op)[s]}") for pl, op in plans for s in pl.active_stages(op)]
 
     def step(events=None):
         for i, (pl, op, s, _) in enumerate(stage_list):
@@ -336,7 +339,7 @@ def verify_batch(args, rd, imgs, enc, marked, rec, maps, etas, payload, bits_out
     import torch
     n, H, W = imgs.shape
     N = H * W
-    lmr = torch.tensor([v == rd.LMR for v in variants], device=imgs.device)
+    lmr = torch.tensor([(v & 1) == rd.LMR for v in variants], device=imgs.device)
     # LMR lossless; EMR differs only in the LSB plane
     exact = (rec == imgs).flatten(1).all(1)
     lsb_only = (((rec ^ imgs) & 0xFE) == 0).flatten(1).all(1)
@@ -527,8 +530,9 @@ def run_c4(args):
     p_ext = rd.Plan([rd.make_job(params[k], H, W, src=marked[k], bits_out=bits[k], max_bits=caps[k], info=info[k],
                                  b=0) for k in range(n)], st)
     p_dec = rd.Plan([rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], info=info[k], b=0) for k in range(n)], st)
-    stages = [(p_ext, rd.OP_EXTRACT, i, nm) for i, nm in enumerate(rd.stages(rd.OP_EXTRACT))] + \
-             [(p_dec, rd.OP_DECRYPT_RECOVER, i, nm) for i, nm in enumerate(rd.stages(rd.OP_DECRYPT_RECOVER))]
+    stages = [(p_ext, rd.OP_EXTRACT, i, rd.stages(rd.OP_EXTRACT)[i]) for i in p_ext.active_stages(rd.OP_EXTRACT)] + \
+             [(p_dec, rd.OP_DECRYPT_RECOVER, i, rd.stages(rd.OP_DECRYPT_RECOVER)[i])
+              for i in p_dec.active_stages(rd.OP_DECRYPT_RECOVER)]
     for _ in range(args.warmup):
         for pl, op, i, _ in stages:
             pl.run_stage(op, i, st)
@@ -757,6 +761,10 @@ def roofline(res, peaks, args):
         "dec_gather_recover": 1.0 * px,                # write I'
         "topmap": 0.0,
     }
+    if getattr(args, "med", False):
+        # MED: the gather pass only stages the de-rotated pixels; the wavefront writes I'
+        hbm_bytes["dec_gather_recover"] = 0.0
+        hbm_bytes["med_wavefront"] = 1.0 * px
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
                 "z2_encrypt": der / 8 * px, "z2_decrypt": der / 8 * px}
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -845,6 +853,9 @@ def main():
     ap.add_argument("--c3-small", type=int, default=256)
     ap.add_argument("--c3-big", type=int, default=4)
     ap.add_argument("--c4-images", type=int, default=64)
+    ap.add_argument("--med", action="store_true",
+                    help="the related-work MED predictor variants (EMR_MED / LMR_MED) instead of the paper's "
+                         "glide; recovery runs as a tiled anti-diagonal wavefront")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -852,8 +863,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     config = {"workload": f"batch of {args.images} synthetic {args.size}x{args.size} uint8 images per GPU, "
-                          "EMR (even) / LMR per-pixel stages (odd), label_encrypt + full-capacity embed + "
-                          "extract + decrypt_recover per step",
+                          + ("EMR_MED (even) / LMR_MED (odd), the related-work MED predictor with wavefront "
+                             "recovery, " if args.med else "EMR (even) / LMR per-pixel stages (odd), ")
+                          + "label_encrypt + full-capacity embed + extract + decrypt_recover per step",
               "images_per_gpu": args.images, "H": args.size, "W": args.size,
               "keystream": "ChaCha20 (RFC 8439)", "parallelism": f"replicas x{args.gpus}",
               "l2": "no flush: each step streams ~1.6 GB (inputs and outputs > 129 MB L2)"}
@@ -867,7 +879,7 @@ def main():
         if rank != 0:
             return
         imgs = make_images(min(args.images, 256), args.size, args.size)
-        cb = oracle_throughput(imgs, 0, budget_s=12.0)
+        cb = oracle_throughput(imgs, 0, budget_s=12.0, med=args.med)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
                 "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config,
@@ -884,7 +896,7 @@ def main():
         return
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = oracle_throughput(args._images, 0, budget_s=10.0)
+        cpu_base = oracle_throughput(args._images, 0, budget_s=10.0, med=args.med)
 
     if world > 1:
         import torch

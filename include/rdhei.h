@@ -59,7 +59,19 @@ enum rdhei_status {
     RDHEI_ESPACE = 5      /* workspace too small */
 };
 
-enum rdhei_variant { RDHEI_EMR = 0, RDHEI_LMR = 1 };
+/* RDHEI_EMR / RDHEI_LMR are the paper's methods: labels compare a pixel's top b bits
+ * with the left neighbour's (the glide of Eqs. gliding1/2).  RDHEI_EMR_MED /
+ * RDHEI_LMR_MED are a RELATED-WORK variant, not the paper's method: labels compare
+ * with the median edge detector (MED, LOCO-I) prediction that Sec. II quotes from
+ * Puyang et al. and Puteaux et al.,
+ *   pred = min(A, B) if C >= max(A, B); max(A, B) if C <= min(A, B); A + B - C else,
+ * A, B, C the left, upper and upper-left neighbours (row 0 predicts from the left,
+ * column 0 from above, pixel (0, 0) is never redundant; the EMR form predicts on the
+ * top seven bits, since the receiver loses the LSB plane).  Everything else (b,
+ * rotation, encryption, hiding) is as in the base variant.  Recovery then depends on
+ * the recovered left, upper and upper-left pixels, so rdhei_decrypt_recover runs it
+ * as a tiled anti-diagonal wavefront (plan stage 3). */
+enum rdhei_variant { RDHEI_EMR = 0, RDHEI_LMR = 1, RDHEI_EMR_MED = 2, RDHEI_LMR_MED = 3 };
 
 /* Per-image results, written by the device into caller-owned device memory. */
 typedef struct rdhei_info {
@@ -77,7 +89,7 @@ typedef struct rdhei_info {
 /* One image of a batch.  Pointers are device pointers; unused ones may be NULL. */
 typedef struct rdhei_job {
     int32_t H, W;
-    int32_t variant;      /* RDHEI_EMR or RDHEI_LMR */
+    int32_t variant;      /* enum rdhei_variant */
     int32_t b;            /* label_encrypt: 0 = choose by Eq. optimal_b (EMR b in [2,7],
                              LMR b in [2,8], ties to the smaller b), else fixed.
                              embed / extract / decrypt_recover: the public b; 0 = read
@@ -161,10 +173,13 @@ void rdhei_plan_destroy(rdhei_plan *plan);
 
 /* The kernels of one operation, one launch per stage, for timing each kernel with
  * events recorded between stages: stage 0 also issues the per-call workspace memsets.
- * rdhei_plan_run(plan, op) == every stage of op in order.  Unknown op: 0 stages. */
+ * rdhei_plan_run(plan, op) == every stage of op in order.  Unknown op: 0 stages.
+ * rdhei_plan_stage_active: 1 when the stage launches work for this plan's jobs (the
+ * MED wavefront stage of rdhei_decrypt_recover launches only for MED variants). */
 int rdhei_plan_stage_count(int op);
 const char *rdhei_stage_name(int op, int stage);
 int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
+int rdhei_plan_stage_active(const rdhei_plan *plan, int op, int stage);
 
 /* ---------------------------------------------------------------------------------
  * Security and quality statistics (Sec. IV-C, Tab. analysis; PSNR and SSIM of the

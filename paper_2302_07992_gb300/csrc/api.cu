@@ -9,14 +9,15 @@
 #include "common.cuh"
 
 namespace rdhei {
-void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st);
+void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStream_t st);
 void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
-void launch_enc_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
-void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st);
+void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
+void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 void launch_count(const Batch& B, bool extract, cudaStream_t st);
 void launch_scan(const Batch& B, bool extract, cudaStream_t st);
 void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st);
 void launch_lmr_side(const Batch& B, cudaStream_t st);
+void launch_med_wave(const Batch& B, cudaStream_t st);
 }  // namespace rdhei
 
 using namespace rdhei;
@@ -25,12 +26,14 @@ struct rdhei_plan {
   std::vector<rdhei_job> jobs;
   std::vector<ImgDesc> desc;
   std::vector<uint32_t> tile_prefix, chunk_prefix, z2_prefix, strip_prefix;
+  std::vector<uint2> wave_list;          // MED recovery tiles in anti-diagonal order
   std::vector<size_t> stash_off, ebuf_off;
   size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
          off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_strip_prefix = 0, off_tile_rows = 0,
-         off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, total = 0;
-  uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0;
-  bool any_lmr = false, general = false;
+         off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, off_wave_flags = 0, off_wave_list = 0,
+         off_lab = 0, total = 0;
+  uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0, total_wave = 0;
+  bool any_lmr = false, general = false, any_med = false;
   void* ws = nullptr;
   Batch batch{};
 };
@@ -46,8 +49,8 @@ static int levels_of(int H, int W) {
 static int validate_job(const rdhei_job& j) {
   if (j.H < 1 || j.W < 1 || j.H > 65536 || j.W > 65536) return RDHEI_EINVAL;
   if ((uint64_t)j.H * (uint64_t)j.W > (1ull << 27)) return RDHEI_EINVAL;
-  if (j.variant != RDHEI_EMR && j.variant != RDHEI_LMR) return RDHEI_EINVAL;
-  const int bmax = j.variant == RDHEI_EMR ? 7 : 8;
+  if (j.variant < RDHEI_EMR || j.variant > RDHEI_LMR_MED) return RDHEI_EINVAL;
+  const int bmax = (j.variant & 1) == RDHEI_EMR ? 7 : 8;
   if (j.b != 0 && (j.b < 2 || j.b > bmax)) return RDHEI_EINVAL;
   if (j.rot_lmin < 0 || j.rot_lmin > 16) return RDHEI_EINVAL;
   if (!j.info) return RDHEI_EINVAL;
@@ -68,6 +71,8 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)p->total_chunks * 8, 256);
   p->off_tile_flags = off;
   off = align_up(off + (size_t)p->total_tiles * 4, 256);
+  p->off_wave_flags = off;
+  off = align_up(off + (size_t)p->total_wave * 4, 256);
   p->zero_bytes = off - p->off_zero;
   p->off_desc = off;
   off = align_up(off + (size_t)n * sizeof(ImgDesc), 256);
@@ -79,6 +84,8 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_strip_prefix = off;
   off = align_up(off + (size_t)(n + 1) * 4, 256);
+  p->off_wave_list = off;
+  off = align_up(off + (size_t)p->total_wave * sizeof(uint2), 256);
   p->off_tile_rows = off;
   off = align_up(off + (size_t)p->total_tiles * 128, 256);
   p->off_subtree = off;
@@ -89,6 +96,8 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)p->total_tiles, 256);
   p->off_tilemap = off;
   off = align_up(off + (size_t)p->total_tiles * sizeof(TileMap), 256);
+  p->off_lab = off;
+  if (p->any_med) off = align_up(off + (size_t)p->total_tiles * AUX_BYTES, 256);
   p->stash_off.resize(n);
   p->ebuf_off.resize(n);
   for (int i = 0; i < n; i++) {
@@ -120,9 +129,10 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     if (rc) { delete p; return rc; }
     ImgDesc& d = p->desc[i];
     std::memset(&d, 0, sizeof(d));
-    d.H = j.H; d.W = j.W; d.variant = j.variant; d.b = j.b;
+    d.H = j.H; d.W = j.W; d.variant = j.variant & 1; d.b = j.b;
+    d.med = j.variant >> 1;
     d.nlev = levels_of(j.H, j.W);
-    int lmin = j.rot_lmin > 0 ? j.rot_lmin : (j.variant == RDHEI_EMR ? 1 : 4);
+    int lmin = j.rot_lmin > 0 ? j.rot_lmin : (d.variant == RDHEI_EMR ? 1 : 4);
     if (d.nlev >= 1 && lmin > d.nlev) lmin = d.nlev;
     d.lmin = j.rot_enable ? lmin : NO_ROTATION;
     d.tiles_x = (uint32_t)((j.W + TILE - 1) / TILE);
@@ -160,8 +170,37 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     // no image holds more than 7 bits per pixel: larger requests are capped there
     d.max_bits = j.max_bits < 7ull * j.H * j.W ? j.max_bits : 7ull * j.H * j.W;
     d.info = j.info;
-    if (j.variant == RDHEI_LMR) p->any_lmr = true;
+    if (d.variant == RDHEI_LMR) p->any_lmr = true;
+    if (d.med) p->any_med = true;
     if (j.W % 64) p->general = true;
+  }
+  // MED recovery tiles, ordered by anti-diagonal (ty + tx) across all images, so every
+  // tile's upper and left neighbours come earlier in the list
+  {
+    uint32_t maxdiag = 0;
+    uint64_t wave = 0;
+    for (int i = 0; i < n; i++) {
+      ImgDesc& d = p->desc[i];
+      if (!d.med) continue;
+      const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
+      d.wave_tx = (uint32_t)((d.W + WAVE_COLS - 1) / WAVE_COLS);
+      d.wave_base = (uint32_t)wave;
+      wave += (uint64_t)wty * d.wave_tx;
+      if (wty + d.wave_tx - 1 > maxdiag) maxdiag = wty + d.wave_tx - 1;
+    }
+    if (wave >= (1ull << 31)) { delete p; return RDHEI_EINVAL; }
+    p->total_wave = (uint32_t)wave;
+    p->wave_list.reserve(wave);
+    for (uint32_t dg = 0; dg < maxdiag; dg++)
+      for (int i = 0; i < n; i++) {
+        const ImgDesc& d = p->desc[i];
+        if (!d.med) continue;
+        const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
+        for (uint32_t ty = 0; ty < wty && ty <= dg; ty++) {
+          const uint32_t tx = dg - ty;
+          if (tx < d.wave_tx) p->wave_list.push_back(make_uint2((uint32_t)i, (ty << 16) | tx));
+        }
+      }
   }
   if (tiles >= (1ull << 32) || chunks >= (1ull << 32) || z2 >= (1ull << 32)) { delete p; return RDHEI_EINVAL; }
   p->tile_prefix[n] = (uint32_t)tiles;
@@ -191,13 +230,15 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
     p->desc[i].ebuf = base + p->ebuf_off[i];
   }
   // one host image of the descriptor region, copied once
-  const size_t lo = p->off_desc, hi = p->off_strip_prefix + (size_t)(n + 1) * 4;
+  const size_t lo = p->off_desc, hi = p->off_wave_list + (size_t)p->total_wave * sizeof(uint2);
   std::vector<uint8_t> host(hi - lo, 0);
   if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
   std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_z2_prefix - lo), p->z2_prefix.data(), (size_t)(n + 1) * 4);
   std::memcpy(host.data() + (p->off_strip_prefix - lo), p->strip_prefix.data(), (size_t)(n + 1) * 4);
+  if (p->total_wave)
+    std::memcpy(host.data() + (p->off_wave_list - lo), p->wave_list.data(), (size_t)p->total_wave * sizeof(uint2));
   if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return RDHEI_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
@@ -223,6 +264,10 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.aux = base + p->off_aux;
   B.sigma6 = base + p->off_sigma6;
   B.tilemap = reinterpret_cast<TileMap*>(base + p->off_tilemap);
+  B.lab = p->any_med ? base + p->off_lab : nullptr;
+  B.wave_flags = reinterpret_cast<uint32_t*>(base + p->off_wave_flags);
+  B.wave_list = reinterpret_cast<const uint2*>(base + p->off_wave_list);
+  B.total_wave = p->total_wave;
   return RDHEI_OK;
 }
 
@@ -230,7 +275,7 @@ static bool aligned4(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 3
 
 static int check_op(const rdhei_plan* p, int op) {
   for (const rdhei_job& j : p->jobs) {
-    const bool lmr = j.variant == RDHEI_LMR;
+    const bool lmr = (j.variant & 1) == RDHEI_LMR;
     switch (op) {
       case RDHEI_OP_LABEL_ENCRYPT:
         if (!j.src || !j.dst) return RDHEI_EINVAL;
@@ -266,8 +311,9 @@ static int check_op(const rdhei_plan* p, int op) {
 
 int rdhei_plan_stage_count(int op) {
   switch (op) {
-    case RDHEI_OP_LABEL_ENCRYPT:
     case RDHEI_OP_DECRYPT_RECOVER:
+      return 4;
+    case RDHEI_OP_LABEL_ENCRYPT:
     case RDHEI_OP_EMBED:
     case RDHEI_OP_EXTRACT:
       return 3;
@@ -280,10 +326,10 @@ int rdhei_plan_stage_count(int op) {
 
 const char* rdhei_stage_name(int op, int stage) {
   static const char* enc[3] = {"pass1_keystream_hist", "topmap", "enc_gather"};
-  static const char* dec[3] = {"pass1_keystream_decrypt", "topmap", "dec_gather_recover"};
+  static const char* dec[4] = {"pass1_keystream_decrypt", "topmap", "dec_gather_recover", "med_wavefront"};
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
-    case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 3 ? dec[stage] : "";
+    case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 4 ? dec[stage] : "";
     case RDHEI_OP_EMBED: return stage == 0 ? "z2_encrypt" : stage == 1 ? "embed_count" : stage == 2 ? "embed_scan" : "";
     case RDHEI_OP_EXTRACT:
       return stage == 0 ? "extract_count" : stage == 1 ? "extract_scan" : stage == 2 ? "z2_decrypt" : "";
@@ -309,16 +355,16 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
         if (j.W % 16 == 0) continue;
         const size_t bytes = (((size_t)j.H * j.W + 31) / 32) * 4;
         if (j.map_bits && cudaMemsetAsync(j.map_bits, 0, bytes, st) != cudaSuccess) return RDHEI_ECUDA;
-        if (j.variant == RDHEI_LMR && j.eta_bits && cudaMemsetAsync(j.eta_bits, 0, bytes, st) != cudaSuccess)
+        if ((j.variant & 1) == RDHEI_LMR && j.eta_bits && cudaMemsetAsync(j.eta_bits, 0, bytes, st) != cudaSuccess)
           return RDHEI_ECUDA;
       }
     }
   }
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT:
-      if (stage == 0) launch_pass1(B, 0, p->general, st);
+      if (stage == 0) launch_pass1(B, 0, p->general, p->any_med, st);
       else if (stage == 1) launch_topmap(B, true, st);
-      else launch_enc_pass2(B, p->any_lmr, st);
+      else launch_enc_pass2(B, p->any_lmr, p->any_med, st);
       break;
     case RDHEI_OP_EMBED:
       if (stage == 0) launch_z2_xor(B, false, st);
@@ -331,15 +377,22 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       else launch_z2_xor(B, true, st);
       break;
     case RDHEI_OP_DECRYPT_RECOVER:
-      if (stage == 0) launch_pass1(B, 1, p->general, st);
+      if (stage == 0) launch_pass1(B, 1, p->general, false, st);
       else if (stage == 1) launch_topmap(B, false, st);
-      else launch_dec_pass2(B, p->any_lmr, st);
+      else if (stage == 2) launch_dec_pass2(B, p->any_lmr, p->any_med, st);
+      else if (p->any_med) launch_med_wave(B, st);
       break;
     case RDHEI_OP_LMR_SET_SIDE:
       launch_lmr_side(B, st);
       break;
   }
   return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
+}
+
+int rdhei_plan_stage_active(const rdhei_plan* p, int op, int stage) {
+  if (!p || stage < 0 || stage >= rdhei_plan_stage_count(op)) return 0;
+  if (op == RDHEI_OP_DECRYPT_RECOVER && stage == 3) return p->any_med ? 1 : 0;
+  return 1;
 }
 
 int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {

@@ -44,8 +44,10 @@ struct ImgDesc {
   void* info;                 // rdhei_info*
   uint8_t* stash;             // N_px bytes: keystream (encode) / decrypted image (decode)
   uint8_t* ebuf;              // hider: the K2-encrypted message, ceil(nbits / 32) words
-  int32_t H, W, variant, b;   // b: 0 = from info (hider / receiver) or auto (owner)
+  int32_t H, W, variant, b;   // variant: RDHEI_EMR / RDHEI_LMR layout; b: 0 = from info or auto
   int32_t lmin, nlev;         // effective smallest level (NO_ROTATION = none), n
+  int32_t med;                // 1: MED predictor (related-work variant) instead of the glide
+  uint32_t wave_base, wave_tx;   // MED recovery: first wavefront tile, wavefront tiles per row
   uint32_t tiles_x, tiles_y, tile_base, chunk_base, nchunks;
   uint32_t k1[8], n1[3], k2[8], n2[3];
 };
@@ -80,7 +82,24 @@ struct Batch {
   uint8_t* aux;                   // total_tiles * AUX_BYTES
   uint8_t* sigma6;                // total_tiles
   TileMap* tilemap;               // total_tiles
+  uint8_t* lab;                   // MED decode: total_tiles * AUX_BYTES de-rotated label bits
+  uint32_t* wave_flags;           // MED decode: total_wave done flags (zeroed per call)
+  const uint2* wave_list;         // MED decode: (image, ty << 16 | tx) in anti-diagonal order
+  uint32_t total_wave;
 };
+
+// MED recovery wavefront tile: 32 rows (one warp lane per row) x 128 columns.
+constexpr int WAVE_ROWS = 32, WAVE_COLS = 128;
+
+// Median edge detector on four bytes at once (related-work predictor, LOCO-I):
+// min(A, B) where C >= max(A, B), max(A, B) where C <= min(A, B), else A + B - C
+// (which then lies between min and max, so the bytewise wrap-around never triggers).
+__device__ __forceinline__ uint32_t med4(uint32_t A, uint32_t Bv, uint32_t C) {
+  const uint32_t mx = __vmaxu4(A, Bv), mn = __vminu4(A, Bv);
+  const uint32_t ge = __vcmpgeu4(C, mx), le = __vcmpleu4(C, mn);
+  const uint32_t lin = __vsub4(__vadd4(A, Bv), C);
+  return (ge & mn) | (~ge & le & mx) | (~ge & ~le & lin);
+}
 
 // Error codes shared with rdhei.h.
 constexpr int ERR_CAPACITY = 2;

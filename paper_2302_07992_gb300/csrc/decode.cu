@@ -13,7 +13,7 @@
 
 namespace rdhei {
 
-template <bool ANY_LMR>
+template <bool ANY_LMR, bool ANY_MED>
 __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t ain[TILE * TPITCH];
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
   const int b = d.b > 0 ? d.b : info->b;
   const bool lmr = ANY_LMR && d.variant == RDHEI_LMR;
+  const bool med = ANY_MED && d.med != 0;
   const uint32_t ty = s - __ldg(B.strip_prefix + img);
   const uint32_t tiles_x = d.tiles_x;
   // the replaced field: EMR top b bits, LMR bits 6 .. 8-b (Sec. III-B-2)
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
     const int x = (int)tx * TILE + 16 * quarter;
     int valid = (y < H) ? min(16, W - x) : 0;
     if (valid < 0) valid = 0;
-    uint32_t v[4], xf[4], mm[4];
+    uint32_t v[4], xf[4], mm[4], labs[4];
     {
       const uint4 v4 = *reinterpret_cast<const uint4*>(tout + row * TPITCH + 16 * quarter);
       const uint4 a4 = *reinterpret_cast<const uint4*>(aout + row * TPITCH + 16 * quarter);
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
         }
         const int nv = valid - 4 * i;                             // pixels past the row end: label 0
         lab &= nv <= 0 ? 0u : nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
-        if (i == 0 && x == 0 && valid > 0) lab |= 1u;             // first image column: non-redundant
+        if (i == 0 && x == 0 && valid > 0 && !med) lab |= 1u;     // first image column: non-redundant
+        if (ANY_MED) labs[i] = lab;
         uint32_t m = lab * 0xFFu;
         uint32_t f = v[i] & FM4 & m;
         f |= ~m & (f << 8);  m |= m << 8;
@@ -140,6 +142,27 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
         carry = (f >> 24) * 0x01010101u;
         carried = (uint32_t)((int32_t)m >> 31);
       }
+    }
+    if (ANY_MED && med) {
+      // MED variant: the prediction needs recovered upper neighbours, so this pass only
+      // writes the decrypted, de-rotated pixels and their labels; the wavefront kernel
+      // restores the fields
+      uint32_t bits16 = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) bits16 |= ((((labs[i] & 0x01010101u) * 0x01020408u) >> 24) & 0xFu) << (4 * i);
+      reinterpret_cast<uint16_t*>(B.lab + (size_t)(d.tile_base + P) * AUX_BYTES)[row * 4 + quarter] = (uint16_t)bits16;
+      if (valid > 0) {
+        uint8_t* dst = d.dst + (size_t)y * W + x;
+        if (valid == 16 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+          *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; k++)
+            if (k < valid) dst[k] = (uint8_t)(v[k >> 2] >> (8 * (k & 3)));
+        }
+      }
+      __syncthreads();
+      continue;
     }
     // 4. carry into my 16 pixels: the last label-1 field of the quarters to my left,
     //    else the strip's carry from the previous tile
@@ -174,10 +197,15 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   }
 }
 
-void launch_dec_pass2(const Batch& B, bool any_lmr, cudaStream_t st) {
+void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_strips == 0) return;
-  if (any_lmr) k_dec_strip<true><<<B.total_strips, 256, 0, st>>>(B);
-  else k_dec_strip<false><<<B.total_strips, 256, 0, st>>>(B);
+  if (any_med) {
+    if (any_lmr) k_dec_strip<true, true><<<B.total_strips, 256, 0, st>>>(B);
+    else k_dec_strip<false, true><<<B.total_strips, 256, 0, st>>>(B);
+  } else {
+    if (any_lmr) k_dec_strip<true, false><<<B.total_strips, 256, 0, st>>>(B);
+    else k_dec_strip<false, false><<<B.total_strips, 256, 0, st>>>(B);
+  }
 }
 
 }  // namespace rdhei

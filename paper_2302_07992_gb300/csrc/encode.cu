@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
 //   4. XOR with the stashed keystream at Q (Eq. image_encryption), LMR side bits
 //      into bit 7, packed rotated maps.
 // ---------------------------------------------------------------------------------
-template <bool ANY_LMR>
+template <bool ANY_LMR, bool ANY_MED>
 __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
   __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
   __shared__ uint32_t selt[16];
   __shared__ uint8_t halo[TILE];
+  __shared__ __align__(16) uint8_t uprow[ANY_MED ? TILE + 16 : 16];   // MED: the row above P, its left corner
 
   const uint32_t g = blockIdx.x;
   const int img = owner_of(B.tile_prefix, B.n_images, g);
@@ -159,6 +160,14 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
       if (y < H) h = px0 > 0 ? __ldg(d.src + (size_t)y * W + px0 - 1) : (uint8_t)((w[0] & 0xFFu) ^ 0xFFu);
       halo[row] = h;
     }
+    if (ANY_MED && d.med && row == 0) {
+      // the row above the tile (and its upper-left corner) for the MED prediction
+      const int uy = py0 - 1;
+#pragma unroll
+      for (int k = 0; k < 16; k++)
+        uprow[16 * quarter + k] = (uy >= 0 && x + k < W) ? __ldg(d.src + (size_t)uy * W + x + k) : (uint8_t)0;
+      if (quarter == 0) uprow[TILE] = (uy >= 0 && px0 > 0) ? __ldg(d.src + (size_t)uy * W + px0 - 1) : (uint8_t)0;
+    }
   }
   __syncthreads();
 
@@ -168,11 +177,34 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
     uint32_t left = quarter == 0 ? (uint32_t)halo[row] : (uint32_t)tin[row * TPITCH + 16 * quarter - 1];
     const uint32_t K = (0x80u - (0x100u >> b)) * 0x01010101u;
     uint32_t lw[4];
+    if (!ANY_MED || !d.med) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-      uint32_t prev = i == 0 ? (left << 24) : w[i - 1];
-      uint32_t dd = w[i] ^ __funnelshift_l(prev, w[i], 8);
-      lw[i] = ((((dd & 0x7F7F7F7Fu) + K) | dd) >> 7) & 0x01010101u;
+      for (int i = 0; i < 4; i++) {
+        uint32_t prev = i == 0 ? (left << 24) : w[i - 1];
+        uint32_t dd = w[i] ^ __funnelshift_l(prev, w[i], 8);
+        lw[i] = ((((dd & 0x7F7F7F7Fu) + K) | dd) >> 7) & 0x01010101u;
+      }
+    } else {
+      // related-work MED prediction from the left, upper and upper-left pixels
+      const int y = py0 + row, x = px0 + 16 * quarter;
+      const bool seven = d.variant == RDHEI_EMR;
+      const uint8_t* ur = row > 0 ? tin + (row - 1) * TPITCH + 16 * quarter : uprow + 16 * quarter;
+      uint32_t ul = quarter > 0 ? ur[-1] : row > 0 ? halo[row - 1] : uprow[TILE];
+      if (px0 == 0 && quarter == 0) left = 0;
+      const uint4 u4 = *reinterpret_cast<const uint4*>(ur);
+      const uint32_t up[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const uint32_t A = __funnelshift_l(i == 0 ? (left << 24) : w[i - 1], w[i], 8);
+        const uint32_t C = __funnelshift_l(i == 0 ? (ul << 24) : up[i - 1], up[i], 8);
+        uint32_t pred = seven ? med4((A >> 1) & 0x7F7F7F7Fu, (up[i] >> 1) & 0x7F7F7F7Fu, (C >> 1) & 0x7F7F7F7Fu) << 1
+                              : med4(A, up[i], C);
+        if (y == 0) pred = seven ? A & 0xFEFEFEFEu : A;                            // row 0: from the left
+        if (i == 0 && x == 0) pred = (pred & 0xFFFFFF00u) | (up[0] & (seven ? 0xFEu : 0xFFu));   // column 0
+        uint32_t dd = w[i] ^ pred;
+        if (i == 0 && x == 0 && y == 0) dd |= 0xFFu;                               // pixel (0, 0)
+        lw[i] = ((((dd & 0x7F7F7F7Fu) + K) | dd) >> 7) & 0x01010101u;
+      }
     }
     __syncthreads();   // every thread has read its left byte
     if (LMR) {
@@ -278,10 +310,15 @@ void launch_topmap(const Batch& B, bool owner, cudaStream_t st) {
   if (B.n_images == 0) return;
   k_topmap<<<B.n_images, 256, 0, st>>>(B, owner ? 1 : 0);
 }
-void launch_enc_pass2(const Batch& B, bool any_lmr, cudaStream_t st) {
+void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_tiles == 0) return;
-  if (any_lmr) k_enc_pass2<true><<<B.total_tiles, 256, 0, st>>>(B);
-  else k_enc_pass2<false><<<B.total_tiles, 256, 0, st>>>(B);
+  if (any_med) {
+    if (any_lmr) k_enc_pass2<true, true><<<B.total_tiles, 256, 0, st>>>(B);
+    else k_enc_pass2<false, true><<<B.total_tiles, 256, 0, st>>>(B);
+  } else {
+    if (any_lmr) k_enc_pass2<true, false><<<B.total_tiles, 256, 0, st>>>(B);
+    else k_enc_pass2<false, false><<<B.total_tiles, 256, 0, st>>>(B);
+  }
 }
 
 }  // namespace rdhei

@@ -56,14 +56,14 @@ uint32_t le32(const uint8_t* p) {
 extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   if (!job) return RDHEI_EINVAL;
   const rdhei_job& j = *job;
-  if (j.H < 1 || j.W < 1 || (j.variant != RDHEI_EMR && j.variant != RDHEI_LMR)) return RDHEI_EINVAL;
+  if (j.H < 1 || j.W < 1 || (j.variant < RDHEI_EMR || j.variant > RDHEI_LMR_MED)) return RDHEI_EINVAL;
   const uint64_t N = (uint64_t)j.H * (uint64_t)j.W;
   if (N > kMaxPixels) return RDHEI_ESPACE;                      // beyond the static scratch
-  const int bmax = j.variant == RDHEI_EMR ? 7 : 8;
+  const int bmax = (j.variant & 1) == RDHEI_EMR ? 7 : 8;
   if (j.b != 0 && (j.b < 2 || j.b > bmax)) return RDHEI_EINVAL;
   if (!j.src || !j.info || (reinterpret_cast<uintptr_t>(j.info) & 7)) return RDHEI_EINVAL;
   if (j.max_bits && (!j.bits_out || (reinterpret_cast<uintptr_t>(j.bits_out) & 3))) return RDHEI_EINVAL;
-  if (j.variant == RDHEI_LMR && (!j.map_bits || (reinterpret_cast<uintptr_t>(j.map_bits) & 3))) return RDHEI_EINVAL;
+  if ((j.variant & 1) == RDHEI_LMR && (!j.map_bits || (reinterpret_cast<uintptr_t>(j.map_bits) & 3))) return RDHEI_EINVAL;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RDHEI_ECUDA;
@@ -83,7 +83,7 @@ extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   d.bits_out = j.bits_out;
   d.max_bits = j.max_bits < 7 * N ? j.max_bits : 7 * N;
   d.info = j.info;
-  d.H = j.H; d.W = j.W; d.variant = j.variant; d.b = j.b;
+  d.H = j.H; d.W = j.W; d.variant = j.variant & 1; d.b = j.b;   // extraction is the same for both predictors
   d.nchunks = (uint32_t)((N + CHUNK_PX - 1) / CHUNK_PX);
   for (int k = 0; k < 8; k++) d.k2[k] = le32(j.k2 + 4 * k);
   for (int k = 0; k < 3; k++) d.n2[k] = le32(j.nonce2 + 4 * k);

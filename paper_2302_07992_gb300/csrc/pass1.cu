@@ -40,7 +40,7 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
   return ((uint64_t)hi << 32) | lo;
 }
 
-template <int MODE, bool GENERAL>
+template <int MODE, bool GENERAL, bool ANY_MED>
 __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   // keystream staging for rows that straddle two ChaCha blocks (W not a multiple of 64)
   __shared__ uint32_t ks_stage[GENERAL ? 64 : 1][33];
@@ -145,17 +145,59 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
     }
     // label histogram: zeros(b) = #pixels whose top b bits equal the left neighbour's
     // (Eqs. gliding1/2 with the left-neighbour form of the map).  The first image
-    // column has no left neighbour and is never redundant.
+    // column has no left neighbour and is never redundant.  MED variant (related
+    // work): the prediction is the median edge detector of the left, upper and
+    // upper-left pixels instead (row 0: left; column 0: upper; pixel (0, 0): none).
     uint32_t left;
     if (len > 0) left = x0 > 0 ? (uint32_t)__ldg(src - 1) : ((px[0] & 0xFFu) ^ 0xFFu);
     else left = 0;
+    const bool med = ANY_MED && d.med != 0 && len > 0;
+    const bool seven = d.variant == 0;                     // EMR predicts on the top seven bits
+    uint32_t up[16], ul = 0;
+    if (med) {
+      if (y > 0) {
+        const uint8_t* us = src - W;
+        if (vec && ((reinterpret_cast<uintptr_t>(us) & 15) == 0)) {
+          const uint4* u4 = reinterpret_cast<const uint4*>(us);
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const uint4 v = __ldg(u4 + q);
+            up[4 * q] = v.x; up[4 * q + 1] = v.y; up[4 * q + 2] = v.z; up[4 * q + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; i++) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+              if (4 * i + k < len) v |= (uint32_t)__ldg(us + 4 * i + k) << (8 * k);
+            up[i] = v;
+          }
+        }
+        ul = x0 > 0 ? (uint32_t)__ldg(us - 1) : 0u;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; i++) up[i] = 0u;
+      }
+      if (x0 == 0) left = 0;
+    }
     uint32_t nz[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) nz[k] = 0;
 #pragma unroll
     for (int i = 0; i < 16; i++) {
       uint32_t prev = i == 0 ? (left << 24) : px[i - 1];
-      uint32_t dd = px[i] ^ __funnelshift_l(prev, px[i], 8);
+      uint32_t pred = __funnelshift_l(prev, px[i], 8);          // left neighbours
+      if (med) {
+        const uint32_t Bw = up[i], C = __funnelshift_l(i == 0 ? (ul << 24) : up[i - 1], up[i], 8);
+        uint32_t m = seven ? med4((pred >> 1) & 0x7F7F7F7Fu, (Bw >> 1) & 0x7F7F7F7Fu, (C >> 1) & 0x7F7F7F7Fu) << 1
+                           : med4(pred, Bw, C);
+        if (y == 0) m = seven ? pred & 0xFEFEFEFEu : pred;      // row 0: from the left
+        if (i == 0 && x0 == 0) m = (m & 0xFFFFFF00u) | (Bw & (seven ? 0xFEu : 0xFFu));   // column 0: from above
+        pred = m;
+      }
+      uint32_t dd = px[i] ^ pred;
+      if (med && i == 0 && x0 == 0 && y == 0) dd |= 0xFFu;       // pixel (0, 0): never redundant
       int valid = len - 4 * i;                    // bytes past the row end count as "differs"
       if (valid < 4) dd |= valid <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (8 * valid));
       uint32_t m = dd & 0x7F7F7F7Fu;
@@ -290,14 +332,19 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 }
 
 // general = some image has W % 64 != 0 or a ragged tile row (rows that straddle blocks)
-void launch_pass1(const Batch& B, int mode, bool general, cudaStream_t st) {
+void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStream_t st) {
   if (B.total_tiles == 0) return;
   if (mode == MODE_ENC) {
-    if (general) k_pass1<MODE_ENC, true><<<B.total_tiles, 64, 0, st>>>(B);
-    else k_pass1<MODE_ENC, false><<<B.total_tiles, 64, 0, st>>>(B);
+    if (any_med) {
+      if (general) k_pass1<MODE_ENC, true, true><<<B.total_tiles, 64, 0, st>>>(B);
+      else k_pass1<MODE_ENC, false, true><<<B.total_tiles, 64, 0, st>>>(B);
+    } else {
+      if (general) k_pass1<MODE_ENC, true, false><<<B.total_tiles, 64, 0, st>>>(B);
+      else k_pass1<MODE_ENC, false, false><<<B.total_tiles, 64, 0, st>>>(B);
+    }
   } else {
-    if (general) k_pass1<MODE_DEC, true><<<B.total_tiles, 64, 0, st>>>(B);
-    else k_pass1<MODE_DEC, false><<<B.total_tiles, 64, 0, st>>>(B);
+    if (general) k_pass1<MODE_DEC, true, false><<<B.total_tiles, 64, 0, st>>>(B);
+    else k_pass1<MODE_DEC, false, false><<<B.total_tiles, 64, 0, st>>>(B);
   }
 }
 

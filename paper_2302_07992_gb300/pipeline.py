@@ -28,7 +28,7 @@ class ImageSet:
         self.marked = [torch.empty_like(x) for x in self.img]
         self.rec = [torch.empty_like(x) for x in self.img]
         N = [x.numel() for x in self.img]
-        lmr = [v == rd.LMR for v in self.variants]
+        lmr = [(v & 1) == rd.LMR for v in self.variants]
         self.maps = [rd.bitbuf(N[i], device) if lmr[i] else None for i in range(self.n)]
         self.etas = [rd.bitbuf(N[i], device) if lmr[i] else None for i in range(self.n)]
         self.side_n = [0] * self.n
@@ -110,7 +110,7 @@ class BatchedPipeline:
         self.graph.replay()
 
     def launches_per_step(self) -> int:
-        return sum(len(rd.stages(op)) for _, op in self.plans)
+        return sum(len(pl.active_stages(op)) for pl, op in self.plans)
 
 
 class PerImagePipeline:
@@ -127,7 +127,7 @@ class PerImagePipeline:
                 pl.run(op, stream)
 
     def launches_per_step(self) -> int:
-        return sum(len(rd.stages(op)) for per in self.plans for _, op in per)
+        return sum(len(pl.active_stages(op)) for per in self.plans for pl, op in per)
 
 
 def default_payload(seed_of):

@@ -16,6 +16,8 @@ import torch
 from . import build as _build
 
 EMR, LMR = 0, 1
+# the related-work variants: MED (LOCO-I) prediction instead of the paper's glide
+EMR_MED, LMR_MED = 2, 3
 OP_LABEL_ENCRYPT, OP_EMBED, OP_EXTRACT, OP_DECRYPT_RECOVER, OP_LMR_SET_SIDE = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE"}
 RDHEI_OK, RDHEI_EINVAL, RDHEI_ECAPACITY, RDHEI_ECUDA, RDHEI_ETIMEOUT, RDHEI_ESPACE = range(6)
@@ -68,6 +70,8 @@ _lib.rdhei_plan_stage_count.argtypes = [ctypes.c_int]
 _lib.rdhei_plan_stage_count.restype = ctypes.c_int
 _lib.rdhei_stage_name.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.rdhei_stage_name.restype = ctypes.c_char_p
+_lib.rdhei_plan_stage_active.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+_lib.rdhei_plan_stage_active.restype = ctypes.c_int
 _lib.rdhei_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.rdhei_plan_destroy.restype = None
 _lib.rdhei_workspace_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
@@ -197,6 +201,10 @@ class Plan:
         _check(_lib.rdhei_plan_run_stage(self._h, int(op), int(stage), _stream(stream)),
                f"rdhei_plan_run_stage({op}, {stage})")
 
+    def active_stages(self, op: int) -> list[int]:
+        """Stages of op that launch work for this plan's jobs."""
+        return [s for s in range(len(stages(op))) if _lib.rdhei_plan_stage_active(self._h, int(op), s)]
+
     def status(self, stream=None) -> int:
         code = ctypes.c_int32(0)
         _check(_lib.rdhei_workspace_status(ctypes.c_void_p(self._ws_ptr), _stream(stream), ctypes.byref(code)),
@@ -243,7 +251,7 @@ def label_encrypt(img: torch.Tensor, p: Params, side_bits: torch.Tensor | None =
     enc = torch.empty_like(img)
     info = new_info(1) if info is None else info
     mb = bitbuf(H * W) if want_maps else None
-    eb = bitbuf(H * W) if (want_maps and p.variant == LMR) else None
+    eb = bitbuf(H * W) if (want_maps and (p.variant & 1) == LMR) else None
     sb = None if side_bits is None else as_bitbuf(side_bits, side_nbits)
     j = make_job(p, H, W, src=img, dst=enc, map_bits=mb, eta_bits=eb, side_bits=sb, side_nbits=side_nbits,
                  info=info)

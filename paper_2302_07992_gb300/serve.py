@@ -99,7 +99,7 @@ class Server:
         imgs = [torch.empty(r.image.shape, dtype=torch.uint8, device=dev) for r in reqs]
         enc = [torch.empty_like(x) for x in imgs]
         marked = [torch.empty_like(x) for x in imgs]
-        lmr = [r.params.variant == rd.LMR for r in reqs]
+        lmr = [(r.params.variant & 1) == rd.LMR for r in reqs]
         maps = [rd.bitbuf(x.numel(), dev) if l else None for x, l in zip(imgs, lmr)]
         etas = [rd.bitbuf(x.numel(), dev) if l else None for x, l in zip(imgs, lmr)]
         pays = [rd.bitbuf(r.nbits, dev) for r in reqs]

@@ -55,8 +55,9 @@ def test_host_validation_without_gpu(lib):
     lib.rdhei_workspace_size.restype = ctypes.c_size_t
     lib.rdhei_workspace_size.argtypes = [ctypes.c_void_p, ctypes.c_int]
     for H, W, var, b, ok in [(512, 512, 0, 0, True), (0, 5, 0, 0, False), (5, 70000, 0, 0, False),
-                             (20000, 20000, 0, 0, False), (8, 8, 2, 0, False), (8, 8, 0, 8, False),
-                             (8, 8, 1, 8, True), (8, 8, 0, 1, False)]:
+                             (20000, 20000, 0, 0, False), (8, 8, 4, 0, False), (8, 8, -1, 0, False),
+                             (8, 8, 0, 8, False), (8, 8, 1, 8, True), (8, 8, 0, 1, False),
+                             (8, 8, 2, 0, True), (8, 8, 3, 8, True), (8, 8, 2, 8, False)]:
         hdr[0], hdr[1], hdr[2], hdr[3], hdr[4], hdr[5] = H, W, var, b, 0, 1
         size = lib.rdhei_workspace_size(ctypes.addressof(j), 1)
         assert (size > 0) == ok, (H, W, var, b)

@@ -35,7 +35,8 @@ def _pipeline(rd, img_np, variant, seed, frac=1.0, side_frac=0.4, **kw):
     p, op = _params(rd, variant, seed, **kw)
     img = torch.from_numpy(img_np).cuda()
     nb = (H * W + 7) // 8
-    side_n = int(H * W * side_frac) if variant == oracle.LMR else 0
+    lmr = (variant & 1) == oracle.LMR
+    side_n = int(H * W * side_frac) if lmr else 0
     side = synth.random_bits(seed, side_n) if side_n else None
     side_t = torch.from_numpy(side).cuda() if side_n else None
 
@@ -45,13 +46,13 @@ def _pipeline(rd, img_np, variant, seed, frac=1.0, side_frac=0.4, **kw):
     assert e["b"] == r.b and e["capacity"] == r.capacity, "b / capacity"
     assert np.array_equal(_np(e["enc"]), r.enc), "encrypted image"
     assert np.array_equal(_np(e["map_bits"], nb), r.map_bits), "rotated location map"
-    if variant == oracle.LMR:
+    if lmr:
         assert np.array_equal(_np(e["eta_bits"], nb), r.eta_bits), "rotated first-MSB map"
 
     nbits = int(r.capacity * frac)
     pay = synth.payload_bits(seed, nbits)
-    lmr_map = e["map_bits"] if variant == oracle.LMR else None
-    lmr_map_np = r.map_bits if variant == oracle.LMR else None
+    lmr_map = e["map_bits"] if lmr else None
+    lmr_map_np = r.map_bits if lmr else None
     m = rd.embed(e["enc"], p, r.b, torch.from_numpy(pay).cuda(), nbits, lmr_map)
     mref, kref = oracle.embed(op, r.b, r.enc, pay, nbits, lmr_map_np)
     assert m["embedded"] == kref
@@ -64,11 +65,11 @@ def _pipeline(rd, img_np, variant, seed, frac=1.0, side_frac=0.4, **kw):
     # the zero padding of the last word is part of the contract
     assert not _np(x["bits"])[(xk + 7) // 8:].any() or xk % 8 == 0
 
-    lmr_eta = e["eta_bits"] if variant == oracle.LMR else None
+    lmr_eta = e["eta_bits"] if lmr else None
     rec = rd.decrypt_recover(m["marked"], p, r.b, lmr_map, lmr_eta)
-    rref = oracle.decrypt_recover(op, r.b, mref, lmr_map_np, r.eta_bits if variant == oracle.LMR else None)
+    rref = oracle.decrypt_recover(op, r.b, mref, lmr_map_np, r.eta_bits if lmr else None)
     assert np.array_equal(_np(rec), rref), "recovered image"
-    if variant == oracle.LMR:
+    if lmr:
         assert np.array_equal(rref, img_np)
     return r
 
