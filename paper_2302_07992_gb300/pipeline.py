@@ -132,3 +132,133 @@ class PerImagePipeline:
 
 def default_payload(seed_of):
     return lambda i, nbits: synth.payload_bits(seed_of(i), nbits)
+
+
+class OverlappedPipeline:
+    """Host-to-host processing of a batch of equal-size images with the copies hidden
+    behind the kernels.  The batch is cut into chunks; each chunk has its own four
+    plans.  Chunk c's inputs (pixels, payload bits, LMR side bits) go up on an upload
+    stream while chunk c - 1 runs the four operations on the compute stream and chunk
+    c - 2's results (recovered pixels, extracted bits) come down on a download stream.
+    Events order the reuse of each chunk's device buffers from one run to the next.
+    Payloads and extracted bits are packed per image to their capacity, so only the
+    bytes that carry bits cross the bus."""
+
+    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda"):
+        self.n, self.H, self.W = n, H, W
+        self.dev = torch.device(device)
+        N = H * W
+        self.variants = list(variants)
+        lmr = [(v & 1) == rd.LMR for v in self.variants]
+        self.caps = [int(c) for c in caps]
+        # per-image offsets into the packed payload / bits buffers (16-byte aligned)
+        self.pay_off, off = [], 0
+        for c in self.caps:
+            self.pay_off.append(off)
+            off += ((c + 127) // 128) * 16
+        self.pay_bytes = max(off, 16)
+        self.side_nbits = [int(side_nbits[i]) if (side_nbits is not None and lmr[i]) else 0 for i in range(n)]
+        self.side_off, off = [], 0
+        for s in self.side_nbits:
+            self.side_off.append(off)
+            off += ((s + 127) // 128) * 16
+        self.side_bytes = max(off, 16)
+        dev = self.dev
+        self.img = torch.empty((n, H, W), dtype=torch.uint8, device=dev)
+        self.enc = torch.empty_like(self.img)
+        self.marked = torch.empty_like(self.img)
+        self.rec = torch.empty_like(self.img)
+        mb = ((N + 31) // 32) * 4
+        self.maps = torch.zeros((n, mb), dtype=torch.uint8, device=dev)
+        self.etas = torch.zeros((n, mb), dtype=torch.uint8, device=dev)
+        self.pay = torch.zeros(self.pay_bytes, dtype=torch.uint8, device=dev)
+        self.bits = torch.zeros(self.pay_bytes, dtype=torch.uint8, device=dev)
+        self.side = torch.zeros(self.side_bytes, dtype=torch.uint8, device=dev)
+        self.info = rd.new_info(n, dev)
+        self.up, self.comp, self.down = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        bounds = np.linspace(0, n, chunks + 1).astype(int)
+        self.chunks = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        self.plans = []
+        for a, b in self.chunks:
+            enc, emb, ext, dec = [], [], [], []
+            for k in range(a, b):
+                p = params[k]
+                m = self.maps[k] if lmr[k] else None
+                pay = self.pay[self.pay_off[k]:]
+                bo = self.bits[self.pay_off[k]:]
+                sd = self.side[self.side_off[k]:] if self.side_nbits[k] else None
+                enc.append(rd.make_job(p, H, W, src=self.img[k], dst=self.enc[k], map_bits=m,
+                                       eta_bits=self.etas[k] if lmr[k] else None, side_bits=sd,
+                                       side_nbits=self.side_nbits[k], info=self.info[k]))
+                emb.append(rd.make_job(p, H, W, src=self.enc[k], dst=self.marked[k], map_bits=m, payload=pay,
+                                       nbits=self.caps[k], info=self.info[k], b=0))
+                ext.append(rd.make_job(p, H, W, src=self.marked[k], map_bits=m, bits_out=bo, max_bits=self.caps[k],
+                                       info=self.info[k], b=0))
+                dec.append(rd.make_job(p, H, W, src=self.marked[k], dst=self.rec[k], map_bits=m,
+                                       eta_bits=self.etas[k] if lmr[k] else None, info=self.info[k], b=0))
+            self.plans.append([(rd.Plan(enc, self.comp), rd.OP_LABEL_ENCRYPT), (rd.Plan(emb, self.comp), rd.OP_EMBED),
+                               (rd.Plan(ext, self.comp), rd.OP_EXTRACT),
+                               (rd.Plan(dec, self.comp), rd.OP_DECRYPT_RECOVER)])
+        nc = len(self.chunks)
+        self.ev_comp = [torch.cuda.Event() for _ in range(nc)]
+        self.ev_down = [torch.cuda.Event() for _ in range(nc)]
+        self.started = False
+
+    def host_buffers(self):
+        """Pinned host buffers of the right sizes: (pixels, payload, side) in and
+        (recovered, bits) out."""
+        n, H, W = self.n, self.H, self.W
+        pin = dict(dtype=torch.uint8, pin_memory=True)
+        return (torch.empty((n, H, W), **pin), torch.zeros(self.pay_bytes, **pin), torch.zeros(self.side_bytes, **pin),
+                torch.empty((n, H, W), **pin), torch.zeros(self.pay_bytes, **pin))
+
+    def pack_payloads(self, h_pay, payloads):
+        for k, p in enumerate(payloads):
+            nb = (self.caps[k] + 7) // 8
+            h_pay[self.pay_off[k]:self.pay_off[k] + nb].copy_(torch.as_tensor(np.asarray(p, np.uint8)[:nb]))
+
+    def pack_side(self, h_side, sides):
+        for k, s in enumerate(sides):
+            if self.side_nbits[k]:
+                nb = (self.side_nbits[k] + 7) // 8
+                h_side[self.side_off[k]:self.side_off[k] + nb].copy_(torch.as_tensor(np.asarray(s, np.uint8)[:nb]))
+
+    def _span(self, offs, sizes, a, b):
+        lo = offs[a]
+        hi = offs[b - 1] + ((sizes[b - 1] + 127) // 128) * 16
+        return lo, hi
+
+    def run(self, h_img, h_pay, h_side, h_rec, h_bits):
+        """Enqueue one host-to-host pass over the batch; returns the download stream
+        (synchronise on it, or record an event)."""
+        for c, (a, b) in enumerate(self.chunks):
+            pl, ph = self._span(self.pay_off, self.caps, a, b)
+            sl, sh = self._span(self.side_off, self.side_nbits, a, b)
+            with torch.cuda.stream(self.up):
+                if self.started:
+                    self.up.wait_event(self.ev_comp[c])       # the previous run's kernels read these buffers
+                self.img[a:b].copy_(h_img[a:b], non_blocking=True)
+                if ph > pl:
+                    self.pay[pl:ph].copy_(h_pay[pl:ph], non_blocking=True)
+                if sh > sl:
+                    self.side[sl:sh].copy_(h_side[sl:sh], non_blocking=True)
+                up_done = torch.cuda.Event()
+                up_done.record(self.up)
+            self.comp.wait_event(up_done)
+            if self.started:
+                self.comp.wait_event(self.ev_down[c])         # results of the previous run are down
+            for plan, op in self.plans[c]:
+                plan.run(op, self.comp)
+            self.ev_comp[c].record(self.comp)
+            with torch.cuda.stream(self.down):
+                self.down.wait_event(self.ev_comp[c])
+                h_rec[a:b].copy_(self.rec[a:b], non_blocking=True)
+                if ph > pl:
+                    h_bits[pl:ph].copy_(self.bits[pl:ph], non_blocking=True)
+                self.ev_down[c].record(self.down)
+        self.started = True
+        return self.down
+
+    def status(self) -> int:
+        codes = [pl.status(self.comp) for per in self.plans for pl, _ in per]
+        return max(codes) if codes else 0

@@ -141,3 +141,48 @@ def test_decode_only_on_oracle_marked_4096(rd):
         rec = rd.decrypt_recover(dm, p, r.b, dmap, deta)
         rref = oracle.decrypt_recover(op, r.b, mref, lm, r.eta_bits if lm is not None else None)
         assert np.array_equal(rec.cpu().numpy(), rref)
+
+
+def test_overlapped_host_pipeline_matches_the_oracle():
+    """Host-to-host runs with copies overlapped across chunks give each image's oracle
+    result, run after run (buffer reuse between runs is ordered by events)."""
+    import torch
+    from paper_2302_07992_gb300 import pipeline as pp
+    from paper_2302_07992_gb300 import rdhei as rd
+    n, H, W = 10, 96, 160
+    variants = [rd.EMR, rd.LMR, rd.EMR_MED, rd.LMR_MED, rd.EMR] * 2
+    imgs = np.stack([synth.synth_image(H, W, 700 + k) for k in range(n)])
+    params, oparams, caps, refs, pays, sides = [], [], [], [], [], []
+    sn = (H * W + 7) // 8
+    for k in range(n):
+        kk = synth.keys(700 + k)
+        common = dict(variant=variants[k], k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"])
+        params.append(rd.Params(**common))
+        oparams.append(oracle.Params(**common))
+        lmr = (variants[k] & 1) == rd.LMR
+        side = synth.random_bits(700 + k, sn) if lmr else None
+        r = oracle.label_encrypt(oparams[k], imgs[k], side, sn if lmr else 0)
+        pay = synth.payload_bits(700 + k, r.capacity)
+        lm = r.map_bits if lmr else None
+        marked, _ = oracle.embed(oparams[k], r.b, r.enc, pay, r.capacity, lm)
+        refs.append(oracle.decrypt_recover(oparams[k], r.b, marked, lm, r.eta_bits if lmr else None))
+        caps.append(r.capacity)
+        pays.append(pay)
+        sides.append(side if lmr else np.zeros(1, np.uint8))
+    op = pp.OverlappedPipeline(n, H, W, variants, params, caps,
+                               side_nbits=[sn if (v & 1) == rd.LMR else 0 for v in variants], chunks=3)
+    h_img, h_pay, h_side, h_rec, h_bits = op.host_buffers()
+    h_img.copy_(torch.from_numpy(imgs))
+    op.pack_payloads(h_pay, pays)
+    op.pack_side(h_side, sides)
+    for _ in range(3):
+        h_rec.zero_()
+        h_bits.zero_()
+        op.run(h_img, h_pay, h_side, h_rec, h_bits).synchronize()
+        torch.cuda.synchronize()
+        for k in range(n):
+            assert np.array_equal(h_rec[k].numpy(), refs[k]), k
+            nb = (caps[k] + 7) // 8
+            o = op.pay_off[k]
+            assert np.array_equal(h_bits[o:o + nb].numpy(), pays[k][:nb]), k
+    assert op.status() == 0
