@@ -53,6 +53,30 @@ class Request:
         return 4 * N + 2 * words + 2 * msg + N + N // 4 + 4096
 
 
+class PinnedPool:
+    """Reusable pinned host buffers in power-of-two size classes.  Allocating pinned
+    memory is a slow driver call; a serving loop that hands results back through
+    pinned buffers recycles them once the caller has consumed a result."""
+
+    def __init__(self):
+        self.free: dict[int, list[torch.Tensor]] = {}
+
+    @staticmethod
+    def _cls(nbytes: int) -> int:
+        return max(4096, 1 << (max(int(nbytes), 1) - 1).bit_length())
+
+    def take(self, shape) -> torch.Tensor:
+        nbytes = int(np.prod(shape)) if len(shape) else 1
+        c = self._cls(nbytes)
+        lst = self.free.get(c)
+        buf = lst.pop() if lst else torch.empty(c, dtype=torch.uint8, pin_memory=True)
+        return buf[:nbytes].view(*shape)
+
+    def give(self, t: torch.Tensor):
+        base = t._base if t._base is not None else t
+        self.free.setdefault(base.numel(), []).append(base)
+
+
 class _Batch:
     def __init__(self, reqs, stream):
         self.reqs = reqs
@@ -63,7 +87,7 @@ class _Batch:
 
 class Server:
     def __init__(self, budget_bytes: float = 40e9, max_batch: int = 64, max_batch_pixels: int = 1 << 27,
-                 streams: int = 4, device: int = 0):
+                 streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None):
         self.budget = float(budget_bytes)
         self.max_batch = max_batch
         self.max_batch_pixels = max_batch_pixels
@@ -74,6 +98,8 @@ class Server:
         self.inflight: list[_Batch] = []
         self.queue: deque[Request] = deque()
         self.completed: list[Request] = []
+        self.pool = pool if pool is not None else PinnedPool()
+        self.consume = None
         self.t0 = None
 
     def now(self) -> float:
@@ -115,17 +141,17 @@ class Server:
         p2.run(rd.OP_EMBED, st)
         outs = []
         for i, r in enumerate(reqs):
-            h = torch.empty(r.image.shape, dtype=torch.uint8, pin_memory=True)
+            h = self.pool.take(tuple(r.image.shape))
             h.copy_(marked[i], non_blocking=True)
             o = {"marked": h}
             if lmr[i]:
-                hm = torch.empty(maps[i].shape, dtype=torch.uint8, pin_memory=True)
-                he = torch.empty(etas[i].shape, dtype=torch.uint8, pin_memory=True)
+                hm = self.pool.take(tuple(maps[i].shape))
+                he = self.pool.take(tuple(etas[i].shape))
                 hm.copy_(maps[i], non_blocking=True)
                 he.copy_(etas[i], non_blocking=True)
                 o.update(map_bits=hm, eta_bits=he)
             outs.append(o)
-        hinfo = torch.empty(info.shape, dtype=torch.uint8, pin_memory=True)
+        hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
         bt.keep += [imgs, enc, marked, maps, etas, pays, p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
@@ -152,12 +178,12 @@ class Server:
         p2.run(rd.OP_DECRYPT_RECOVER, st)
         outs = []
         for i, r in enumerate(reqs):
-            hb = torch.empty(bits[i].shape, dtype=torch.uint8, pin_memory=True)
-            hr = torch.empty(r.image.shape, dtype=torch.uint8, pin_memory=True)
+            hb = self.pool.take(tuple(bits[i].shape))
+            hr = self.pool.take(tuple(r.image.shape))
             hb.copy_(bits[i], non_blocking=True)
             hr.copy_(rec[i], non_blocking=True)
             outs.append({"bits": hb, "recovered": hr})
-        hinfo = torch.empty(info.shape, dtype=torch.uint8, pin_memory=True)
+        hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
         bt.keep += [imgs, rec, maps, etas, bits, p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
@@ -170,11 +196,14 @@ class Server:
                 bt.event.synchronize()
                 t = self.now()
                 infos = rd.read_info(bt.hinfo)
+                self.pool.give(bt.hinfo)
                 for r, o, inf in zip(bt.reqs, bt.outs, infos):
                     r.result = {**o, "info": inf}
                     r.done = t
                     self.in_use -= r.device_bytes()
                     self.completed.append(r)
+                    if self.consume is not None:
+                        self.consume(r)
                 self.free_streams.append(bt.stream)
                 block = False
             else:
@@ -200,9 +229,20 @@ class Server:
             px += r.pixels
         return batch
 
-    def run(self, requests: list[Request], realtime: bool = True) -> list[Request]:
+    def release(self, r: Request):
+        """Give a completed request's pinned result buffers back for reuse; the result
+        tensors must not be read afterwards."""
+        for v in list(r.result.values()):
+            if isinstance(v, torch.Tensor) and v.is_pinned():
+                self.pool.give(v)
+        r.result = {"info": r.result.get("info")}
+
+    def run(self, requests: list[Request], realtime: bool = True, consume=None) -> list[Request]:
         """Serve requests whose `arrival` is on the server clock (seconds from start).
-        realtime=False admits everything at once (arrival times ignored)."""
+        realtime=False admits everything at once (arrival times ignored).  consume(r),
+        if given, is called as each request completes (e.g. to hand the result on and
+        release its buffers)."""
+        self.consume = consume
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         self.t0 = time.perf_counter()
         if not realtime:
