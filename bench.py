@@ -241,7 +241,20 @@ def run_gpu(args, rank, world, local_rank):
                                     max_bits=caps[k], info=info[k], b=0))
         dec_jobs.append(rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], map_bits=m,
                                     eta_bits=etas[k] if lmr else None, info=info[k], b=0))
-    plan_emb, plan_ext, plan_dec = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream), rd.Plan(dec_jobs, stream)
+    tuning = None
+    wave_cols = None
+    if args.med:
+        # MED wavefront tile width from the autotuner (cached per device and batch shape);
+        # the encrypted images stand in for the marked ones while tuning
+        from paper_2302_07992_gb300 import tune
+        tune_jobs = [rd.make_job(params[k], H, W, src=enc[k], dst=rec[k],
+                                 map_bits=maps[k] if (variants[k] & 1) == rd.LMR else None,
+                                 eta_bits=etas[k] if (variants[k] & 1) == rd.LMR else None, info=info[k], b=0)
+                     for k in range(n)]
+        wave_cols, times = tune.best_wave_cols(tune_jobs, stream)
+        tuning = {"wave_cols": wave_cols, "ms_per_width": times}
+    plan_emb, plan_ext = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream)
+    plan_dec = rd.Plan(dec_jobs, stream, wave_cols=wave_cols)
     plans = [(plan_enc, rd.OP_LABEL_ENCRYPT), (plan_emb, rd.OP_EMBED), (plan_ext, rd.OP_EXTRACT),
              (plan_dec, rd.OP_DECRYPT_RECOVER)]
     stage_list = [(pl, op, s, f"{rd.stages(op)[s]}") for pl, op in plans for s in pl.active_stages(op)]
@@ -291,15 +304,15 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the public API with host buffers: H2D inputs, four calls,
     # D2H results, every step
-    e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec)
+    e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec, wave_cols)
 
     clocks = clk.summary()
     return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "px_step": px_step,
             "verify": verify, "e2e": e2e, "clocks": clocks, "stage_list": [x[3] for x in stage_list],
-            "caps": caps, "variants": variants}
+            "caps": caps, "variants": variants, "tuning": tuning}
 
 
-def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec_ref):
+def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec_ref, wave_cols=None):
     """The same batch host to host through the public API: pixels, payload bits and
     LMR side bits go up from pinned memory, the four operations run, recovered pixels
     and extracted bits come down -- every step.  The batch is cut into chunks whose
@@ -309,7 +322,7 @@ def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_n
     sn = side_nbits(H, W)
     lmr = [(v & 1) == rd.LMR for v in variants]
     op = pp.OverlappedPipeline(n, H, W, variants, params, caps, side_nbits=[sn if l else 0 for l in lmr],
-                               chunks=args.e2e_chunks, device=dev)
+                               chunks=args.e2e_chunks, device=dev, wave_cols=wave_cols)
     h_img, h_pay, h_side, h_rec, h_bits = op.host_buffers()
     h_img.copy_(torch.from_numpy(imgs_np))
     op.pack_payloads(h_pay, [pay_np[k] for k in range(n)])
@@ -516,9 +529,10 @@ def run_c4(args):
     dev = torch.device("cuda", 0)
     seeds = [synth.image_seed(BASE_SEED + 1, 30_000 + k) for k in range(n)]
     params = []
+    variant = rd.EMR_MED if args.med else rd.EMR
     for k in range(n):
         kk = synth.keys(seeds[k])
-        params.append(rd.Params(variant=rd.EMR, k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"]))
+        params.append(rd.Params(variant=variant, k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"]))
     imgs = torch.from_numpy(np.stack(imgs_np)).to(dev)
     del imgs_np
     enc, marked, rec = torch.empty_like(imgs), torch.empty_like(imgs), torch.empty_like(imgs)
@@ -539,7 +553,15 @@ def run_c4(args):
     bits = torch.zeros((n, pb), dtype=torch.uint8, device=dev)
     p_ext = rd.Plan([rd.make_job(params[k], H, W, src=marked[k], bits_out=bits[k], max_bits=caps[k], info=info[k],
                                  b=0) for k in range(n)], st)
-    p_dec = rd.Plan([rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], info=info[k], b=0) for k in range(n)], st)
+    dec_jobs = [rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], info=info[k], b=0) for k in range(n)]
+    tuning = None
+    wave_cols = None
+    if args.med:
+        # the MED wavefront's tile width, swept by the autotuner on this batch
+        from paper_2302_07992_gb300 import tune
+        wave_cols, times = tune.best_wave_cols(dec_jobs, st)
+        tuning = {"wave_cols": wave_cols, "ms_per_width": times}
+    p_dec = rd.Plan(dec_jobs, st, wave_cols=wave_cols)
     stages = [(p_ext, rd.OP_EXTRACT, i, rd.stages(rd.OP_EXTRACT)[i]) for i in p_ext.active_stages(rd.OP_EXTRACT)] + \
              [(p_dec, rd.OP_DECRYPT_RECOVER, i, rd.stages(rd.OP_DECRYPT_RECOVER)[i])
               for i in p_dec.active_stages(rd.OP_DECRYPT_RECOVER)]
@@ -568,10 +590,12 @@ def run_c4(args):
     # compulsory bytes of the two calls: extract reads I_e' and writes DER/8 B of bits,
     # decrypt_recover reads I_e' and writes I'
     algo = (3.0 + der / 8) * n * N
-    return {"metric": "Mpixel/s decode (extract + decrypt_recover, bit-exact)", "value": n * N / (ms / 1e3) / 1e6,
+    out_extra = {"tuning": tuning} if tuning else {}
+    return {**out_extra, "metric": "Mpixel/s decode (extract + decrypt_recover, bit-exact)", "value": n * N / (ms / 1e3) / 1e6,
             "unit": "Mpixel/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"{n} marked encrypted 4096x4096 EMR images, full-capacity payload "
+            "config": {"workload": f"{n} marked encrypted 4096x4096 {'EMR_MED' if args.med else 'EMR'} images, "
+                                   f"full-capacity payload "
                                    f"(mean DER {der:.3f} bpp); extract + decrypt_recover per step",
                        "l2": "no flush: each step streams > 2 GB"},
             "per_stage_ms": per, "algorithmic_gbs": algo / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm,
@@ -926,6 +950,8 @@ def main():
             "hbm_roofline_mpx": peaks.get("hbm_gbs", 6777.0) * 1e3 / (4.0 + 2 * res["verify"]["mean_der_bpp"] / 8),
             "verify": res["verify"],
             "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()}}
+    if res.get("tuning"):
+        line["tuning"] = res["tuning"]
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -181,6 +181,13 @@ const char *rdhei_stage_name(int op, int stage);
 int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
 int rdhei_plan_stage_active(const rdhei_plan *plan, int op, int stage);
 
+/* Tile width of the MED recovery wavefront (64, 128 = default, or 256 columns; 32 rows):
+ * narrow tiles give more tiles per anti-diagonal, wide ones fewer idle lanes in each
+ * tile's diagonal ramp.  Call after rdhei_plan_create and BEFORE
+ * rdhei_plan_workspace_size / rdhei_plan_upload (it changes the layout).  Returns
+ * RDHEI_EINVAL for another width or an uploaded plan. */
+int rdhei_plan_set_wave_cols(rdhei_plan *plan, int cols);
+
 /* ---------------------------------------------------------------------------------
  * Security and quality statistics (Sec. IV-C, Tab. analysis; PSNR and SSIM of the
  * reconstructed image, Sec. IV) for a batch of 8-bit images:

@@ -33,6 +33,7 @@ struct rdhei_plan {
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, off_wave_flags = 0, off_wave_list = 0,
          off_lab = 0, total = 0;
   uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0, total_wave = 0;
+  int wave_cols = WAVE_COLS_DEFAULT;
   bool any_lmr = false, general = false, any_med = false;
   void* ws = nullptr;
   Batch batch{};
@@ -55,6 +56,39 @@ static int validate_job(const rdhei_job& j) {
   if (j.rot_lmin < 0 || j.rot_lmin > 16) return RDHEI_EINVAL;
   if (!j.info) return RDHEI_EINVAL;
   if (reinterpret_cast<uintptr_t>(j.info) & 7) return RDHEI_EINVAL;
+  return RDHEI_OK;
+}
+
+// MED recovery tiles (32 x wave_cols), ordered by anti-diagonal (ty + tx) across all
+// images, so every tile's upper and left neighbours come earlier in the list.
+static int layout_wave(rdhei_plan* p) {
+  const int n = (int)p->jobs.size();
+  const uint32_t wc = (uint32_t)p->wave_cols;
+  uint32_t maxdiag = 0;
+  uint64_t wave = 0;
+  for (int i = 0; i < n; i++) {
+    ImgDesc& d = p->desc[i];
+    if (!d.med) continue;
+    const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
+    d.wave_tx = (uint32_t)((d.W + wc - 1) / wc);
+    d.wave_base = (uint32_t)wave;
+    wave += (uint64_t)wty * d.wave_tx;
+    if (wty + d.wave_tx - 1 > maxdiag) maxdiag = wty + d.wave_tx - 1;
+  }
+  if (wave >= (1ull << 31)) return RDHEI_EINVAL;
+  p->total_wave = (uint32_t)wave;
+  p->wave_list.clear();
+  p->wave_list.reserve(wave);
+  for (uint32_t dg = 0; dg < maxdiag; dg++)
+    for (int i = 0; i < n; i++) {
+      const ImgDesc& d = p->desc[i];
+      if (!d.med) continue;
+      const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
+      for (uint32_t ty = 0; ty < wty && ty <= dg; ty++) {
+        const uint32_t tx = dg - ty;
+        if (tx < d.wave_tx) p->wave_list.push_back(make_uint2((uint32_t)i, (ty << 16) | tx));
+      }
+    }
   return RDHEI_OK;
 }
 
@@ -174,34 +208,7 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     if (d.med) p->any_med = true;
     if (j.W % 64) p->general = true;
   }
-  // MED recovery tiles, ordered by anti-diagonal (ty + tx) across all images, so every
-  // tile's upper and left neighbours come earlier in the list
-  {
-    uint32_t maxdiag = 0;
-    uint64_t wave = 0;
-    for (int i = 0; i < n; i++) {
-      ImgDesc& d = p->desc[i];
-      if (!d.med) continue;
-      const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
-      d.wave_tx = (uint32_t)((d.W + WAVE_COLS - 1) / WAVE_COLS);
-      d.wave_base = (uint32_t)wave;
-      wave += (uint64_t)wty * d.wave_tx;
-      if (wty + d.wave_tx - 1 > maxdiag) maxdiag = wty + d.wave_tx - 1;
-    }
-    if (wave >= (1ull << 31)) { delete p; return RDHEI_EINVAL; }
-    p->total_wave = (uint32_t)wave;
-    p->wave_list.reserve(wave);
-    for (uint32_t dg = 0; dg < maxdiag; dg++)
-      for (int i = 0; i < n; i++) {
-        const ImgDesc& d = p->desc[i];
-        if (!d.med) continue;
-        const uint32_t wty = (uint32_t)((d.H + WAVE_ROWS - 1) / WAVE_ROWS);
-        for (uint32_t ty = 0; ty < wty && ty <= dg; ty++) {
-          const uint32_t tx = dg - ty;
-          if (tx < d.wave_tx) p->wave_list.push_back(make_uint2((uint32_t)i, (ty << 16) | tx));
-        }
-      }
-  }
+  if (layout_wave(p) != RDHEI_OK) { delete p; return RDHEI_EINVAL; }
   if (tiles >= (1ull << 32) || chunks >= (1ull << 32) || z2 >= (1ull << 32)) { delete p; return RDHEI_EINVAL; }
   p->tile_prefix[n] = (uint32_t)tiles;
   p->chunk_prefix[n] = (uint32_t)chunks;
@@ -268,6 +275,7 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.wave_flags = reinterpret_cast<uint32_t*>(base + p->off_wave_flags);
   B.wave_list = reinterpret_cast<const uint2*>(base + p->off_wave_list);
   B.total_wave = p->total_wave;
+  B.wave_cols = p->wave_cols;
   return RDHEI_OK;
 }
 
@@ -380,13 +388,28 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       if (stage == 0) launch_pass1(B, 1, p->general, false, st);
       else if (stage == 1) launch_topmap(B, false, st);
       else if (stage == 2) launch_dec_pass2(B, p->any_lmr, p->any_med, st);
-      else if (p->any_med) launch_med_wave(B, st);
+      else if (p->any_med) {
+        // the wavefront owns its ticket and done flags: clear them so the stage can rerun
+        uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
+        if (cudaMemsetAsync(base + p->off_wave_flags, 0, (size_t)p->total_wave * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(base + p->off_tickets + 7 * 4, 0, 4, st) != cudaSuccess)
+          return RDHEI_ECUDA;
+        launch_med_wave(B, st);
+      }
       break;
     case RDHEI_OP_LMR_SET_SIDE:
       launch_lmr_side(B, st);
       break;
   }
   return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
+}
+
+int rdhei_plan_set_wave_cols(rdhei_plan* p, int cols) {
+  if (!p || p->ws || (cols != 64 && cols != 128 && cols != 256)) return RDHEI_EINVAL;
+  p->wave_cols = cols;
+  if (layout_wave(p) != RDHEI_OK) return RDHEI_EINVAL;
+  build_layout(p);
+  return RDHEI_OK;
 }
 
 int rdhei_plan_stage_active(const rdhei_plan* p, int op, int stage) {

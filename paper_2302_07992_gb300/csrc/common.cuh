@@ -86,10 +86,11 @@ struct Batch {
   uint32_t* wave_flags;           // MED decode: total_wave done flags (zeroed per call)
   const uint2* wave_list;         // MED decode: (image, ty << 16 | tx) in anti-diagonal order
   uint32_t total_wave;
+  int32_t wave_cols;              // MED decode: wavefront tile width (64, 128 or 256)
 };
 
-// MED recovery wavefront tile: 32 rows (one warp lane per row) x 128 columns.
-constexpr int WAVE_ROWS = 32, WAVE_COLS = 128;
+// MED recovery wavefront tile: 32 rows (one warp lane per row) x wave_cols columns.
+constexpr int WAVE_ROWS = 32, WAVE_COLS_DEFAULT = 128;
 
 // Median edge detector on four bytes at once (related-work predictor, LOCO-I):
 // min(A, B) where C >= max(A, B), max(A, B) where C <= min(A, B), else A + B - C

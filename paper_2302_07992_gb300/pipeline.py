@@ -144,7 +144,7 @@ class OverlappedPipeline:
     Payloads and extracted bits are packed per image to their capacity, so only the
     bytes that carry bits cross the bus."""
 
-    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda"):
+    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda", wave_cols=None):
         self.n, self.H, self.W = n, H, W
         self.dev = torch.device(device)
         N = H * W
@@ -198,7 +198,7 @@ class OverlappedPipeline:
                                        eta_bits=self.etas[k] if lmr[k] else None, info=self.info[k], b=0))
             self.plans.append([(rd.Plan(enc, self.comp), rd.OP_LABEL_ENCRYPT), (rd.Plan(emb, self.comp), rd.OP_EMBED),
                                (rd.Plan(ext, self.comp), rd.OP_EXTRACT),
-                               (rd.Plan(dec, self.comp), rd.OP_DECRYPT_RECOVER)])
+                               (rd.Plan(dec, self.comp, wave_cols=wave_cols), rd.OP_DECRYPT_RECOVER)])
         nc = len(self.chunks)
         self.ev_comp = [torch.cuda.Event() for _ in range(nc)]
         self.ev_down = [torch.cuda.Event() for _ in range(nc)]

@@ -72,6 +72,8 @@ _lib.rdhei_stage_name.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.rdhei_stage_name.restype = ctypes.c_char_p
 _lib.rdhei_plan_stage_active.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
 _lib.rdhei_plan_stage_active.restype = ctypes.c_int
+_lib.rdhei_plan_set_wave_cols.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.rdhei_plan_set_wave_cols.restype = ctypes.c_int
 _lib.rdhei_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.rdhei_plan_destroy.restype = None
 _lib.rdhei_workspace_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
@@ -179,11 +181,15 @@ def read_info(info: torch.Tensor) -> list[dict]:
 class Plan:
     """A validated, uploaded batch: ``run(op)`` launches kernels only (capturable)."""
 
-    def __init__(self, jobs: list[Job], stream=None, workspace: torch.Tensor | None = None):
+    def __init__(self, jobs: list[Job], stream=None, workspace: torch.Tensor | None = None,
+                 wave_cols: int | None = None):
         self._jobs = (Job * len(jobs))(*jobs)
         h = ctypes.c_void_p()
         _check(_lib.rdhei_plan_create(self._jobs, len(jobs), ctypes.byref(h)), "rdhei_plan_create")
         self._h = h
+        if wave_cols is not None:
+            _check(_lib.rdhei_plan_set_wave_cols(h, int(wave_cols)), "rdhei_plan_set_wave_cols")
+        self.wave_cols = wave_cols
         need = _lib.rdhei_plan_workspace_size(h)
         if workspace is None or workspace.numel() < need:
             workspace = torch.empty(max(int(need), 256) + 256, dtype=torch.uint8, device="cuda")

@@ -89,3 +89,57 @@ def test_mixed_batch_in_one_plan(rd):
     dec_plan = [pl for pl, op in bp.plans if op == rd.OP_DECRYPT_RECOVER][0]
     assert 3 in dec_plan.active_stages(rd.OP_DECRYPT_RECOVER)
     assert dec_plan.status() == 0
+
+
+@pytest.mark.parametrize("cols", [64, 128, 256])
+def test_wave_widths_agree(rd, cols):
+    """Every wavefront tile width recovers the oracle's image; the wavefront stage can
+    be rerun on restaged pixels (it clears its own flags and ticket)."""
+    H, W = 200, 530
+    img = synth.synth_image(H, W, 61)
+    for variant in (oracle.EMR_MED, oracle.LMR_MED):
+        k = synth.keys(61)
+        common = dict(variant=variant, k1=k["k1"], nonce1=k["nonce1"], k2=k["k2"], nonce2=k["nonce2"])
+        p, op = rd.Params(**common), oracle.Params(**common)
+        lmr = (variant & 1) == rd.LMR
+        e = oracle.label_encrypt(op, img)
+        pay = synth.payload_bits(61, e.capacity)
+        lm = e.map_bits if lmr else None
+        marked, _ = oracle.embed(op, e.b, e.enc, pay, e.capacity, lm)
+        ref = oracle.decrypt_recover(op, e.b, marked, lm, e.eta_bits if lmr else None)
+        dev_marked = torch.from_numpy(marked).cuda()
+        out = torch.empty_like(dev_marked)
+        mb = rd.as_bitbuf(torch.from_numpy(e.map_bits), H * W) if lmr else None
+        eb = rd.as_bitbuf(torch.from_numpy(e.eta_bits), H * W) if lmr else None
+        info = rd.new_info(1)
+        job = rd.make_job(p, H, W, src=dev_marked, dst=out, map_bits=mb, eta_bits=eb, info=info, b=e.b)
+        plan = rd.Plan([job], wave_cols=cols)
+        plan.run(rd.OP_DECRYPT_RECOVER)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+        for _ in range(2):
+            plan.run_stage(rd.OP_DECRYPT_RECOVER, 2)
+            plan.run_stage(rd.OP_DECRYPT_RECOVER, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert plan.status() == 0
+
+
+def test_autotuner_picks_and_caches_a_width(rd):
+    from paper_2302_07992_gb300 import tune
+    H, W = 256, 512
+    jobs, keep = [], []
+    for i in range(4):
+        img = synth.synth_image(H, W, 80 + i)
+        k = synth.keys(80 + i)
+        p = rd.Params(variant=rd.EMR_MED, k1=k["k1"], nonce1=k["nonce1"], k2=k["k2"], nonce2=k["nonce2"])
+        e = rd.label_encrypt(torch.from_numpy(img).cuda(), p)
+        out = torch.empty_like(e["enc"])
+        info = rd.new_info(1)
+        keep += [e, out, info]
+        jobs.append(rd.make_job(p, H, W, src=e["enc"], dst=out, info=info, b=e["b"]))
+    best, times = tune.best_wave_cols(jobs, refresh=True)
+    assert best in tune.WAVE_WIDTHS and set(times) == {str(c) for c in tune.WAVE_WIDTHS}
+    assert all(v > 0 for v in times.values())
+    again, cached = tune.best_wave_cols(jobs)
+    assert again == best and cached == times
