@@ -138,19 +138,22 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_count(Batch B) {
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint32_t* cnt = reinterpret_cast<uint32_t*>(B.chunk_status);
-  uint32_t g = blockIdx.x;
-  if (g >= B.total_chunks) return;
+  // a contiguous range of chunks per CTA: the owning image only ever steps forward
+  const uint32_t per = (B.total_chunks + gridDim.x - 1) / gridDim.x;
+  uint32_t g = blockIdx.x * per;
+  const uint32_t gend = (uint32_t)umin64((uint64_t)g + per, B.total_chunks);
+  if (g >= gend) return;
   int img = owner_of(B.chunk_prefix, B.n_images, g);
   ChunkPx cur;
   issue_chunk(B.desc[img], g - B.desc[img].chunk_base, t, false, cur);
-  while (g < B.total_chunks) {
+  while (g < gend) {
     const ImgDesc& d = B.desc[img];
     const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
-    const uint32_t gn = g + gridDim.x;
+    const uint32_t gn = g + 1;
     int imgn = img;
     ChunkPx nxt;
-    if (gn < B.total_chunks) {
-      imgn = owner_of(B.chunk_prefix, B.n_images, gn);
+    if (gn < gend) {
+      while (gn >= __ldg(B.chunk_prefix + imgn + 1)) imgn++;
       issue_chunk(B.desc[imgn], gn - B.desc[imgn].chunk_base, t, false, nxt);
     }
     uint32_t v = (uint32_t)__popc(zero_mask(d, cur)) * (uint32_t)slots_of(d, info);
@@ -214,7 +217,8 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_offsets(Batch B) {
   }
 }
 
-// Pass 2 of the payload scan (persistent, grid-stride, next chunk prefetched).
+// Pass 2 of the payload scan (persistent over a contiguous chunk range, next chunk
+// prefetched).
 // Hider: the K2-encrypted message bits of each chunk's slot range go into its slots,
 // first bit into bit 7 (EMR) or 6 (LMR).  Receiver: the slots are concatenated; words
 // inside the chunk's range are stored, words shared with a neighbour are OR-ed (they
@@ -230,14 +234,17 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
   __syncthreads();
   const uint32_t* cnt = reinterpret_cast<const uint32_t*>(B.chunk_status);
   const uint32_t* off = cnt + B.total_chunks;
-  uint32_t g = blockIdx.x;
-  if (g >= B.total_chunks) return;
+  // a contiguous range of chunks per CTA: the owning image only ever steps forward
+  const uint32_t per = (B.total_chunks + gridDim.x - 1) / gridDim.x;
+  uint32_t g = blockIdx.x * per;
+  const uint32_t gend = (uint32_t)umin64((uint64_t)g + per, B.total_chunks);
+  if (g >= gend) return;
   int img = owner_of(B.chunk_prefix, B.n_images, g);
   ChunkPx cur;
   issue_chunk(B.desc[img], g - B.desc[img].chunk_base, t, true, cur);
   uint64_t G = off[g];
   uint32_t T = cnt[g];
-  while (g < B.total_chunks) {
+  while (g < gend) {
     const ImgDesc& d = B.desc[img];
     const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
     const uint32_t slots = (uint32_t)slots_of(d, info);
@@ -262,13 +269,13 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
       }
     }
     // next chunk in flight
-    const uint32_t gn = g + gridDim.x;
+    const uint32_t gn = g + 1;
     int imgn = img;
     ChunkPx nxt;
     uint64_t Gn = 0;
     uint32_t Tn = 0;
-    if (gn < B.total_chunks) {
-      imgn = owner_of(B.chunk_prefix, B.n_images, gn);
+    if (gn < gend) {
+      while (gn >= __ldg(B.chunk_prefix + imgn + 1)) imgn++;
       issue_chunk(B.desc[imgn], gn - B.desc[imgn].chunk_base, t, true, nxt);
       Gn = off[gn];
       Tn = cnt[gn];
