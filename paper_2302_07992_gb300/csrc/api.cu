@@ -27,11 +27,12 @@ struct rdhei_plan {
   std::vector<ImgDesc> desc;
   std::vector<uint32_t> tile_prefix, chunk_prefix, z2_prefix, strip_prefix;
   std::vector<uint2> wave_list;          // MED recovery tiles in anti-diagonal order
+  std::vector<uint32_t> tile_owner, strip_owner;   // image of each global tile / strip
   std::vector<size_t> stash_off, ebuf_off;
   size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
          off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_strip_prefix = 0, off_tile_rows = 0,
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, off_wave_flags = 0, off_wave_list = 0,
-         off_lab = 0, total = 0;
+         off_lab = 0, off_tile_owner = 0, off_strip_owner = 0, total = 0;
   uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0, total_wave = 0;
   int wave_cols = WAVE_COLS_DEFAULT;
   bool any_lmr = false, general = false, any_med = false;
@@ -120,6 +121,10 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)(n + 1) * 4, 256);
   p->off_wave_list = off;
   off = align_up(off + (size_t)p->total_wave * sizeof(uint2), 256);
+  p->off_tile_owner = off;
+  off = align_up(off + (size_t)p->total_tiles * 4, 256);
+  p->off_strip_owner = off;
+  off = align_up(off + (size_t)p->total_strips * 4, 256);
   p->off_tile_rows = off;
   off = align_up(off + (size_t)p->total_tiles * 128, 256);
   p->off_subtree = off;
@@ -218,6 +223,12 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
   p->total_z2 = (uint32_t)z2;
   p->total_tiles = (uint32_t)tiles;
   p->total_chunks = (uint32_t)chunks;
+  p->tile_owner.resize(p->total_tiles);
+  p->strip_owner.resize(p->total_strips);
+  for (int i = 0; i < n; i++) {
+    for (uint32_t t = p->tile_prefix[i]; t < p->tile_prefix[i + 1]; t++) p->tile_owner[t] = (uint32_t)i;
+    for (uint32_t t = p->strip_prefix[i]; t < p->strip_prefix[i + 1]; t++) p->strip_owner[t] = (uint32_t)i;
+  }
   build_layout(p);
   *out = p;
   return RDHEI_OK;
@@ -237,7 +248,7 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
     p->desc[i].ebuf = base + p->ebuf_off[i];
   }
   // one host image of the descriptor region, copied once
-  const size_t lo = p->off_desc, hi = p->off_wave_list + (size_t)p->total_wave * sizeof(uint2);
+  const size_t lo = p->off_desc, hi = p->off_strip_owner + (size_t)p->total_strips * 4;
   std::vector<uint8_t> host(hi - lo, 0);
   if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
   std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
@@ -246,6 +257,10 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   std::memcpy(host.data() + (p->off_strip_prefix - lo), p->strip_prefix.data(), (size_t)(n + 1) * 4);
   if (p->total_wave)
     std::memcpy(host.data() + (p->off_wave_list - lo), p->wave_list.data(), (size_t)p->total_wave * sizeof(uint2));
+  if (p->total_tiles)
+    std::memcpy(host.data() + (p->off_tile_owner - lo), p->tile_owner.data(), (size_t)p->total_tiles * 4);
+  if (p->total_strips)
+    std::memcpy(host.data() + (p->off_strip_owner - lo), p->strip_owner.data(), (size_t)p->total_strips * 4);
   if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return RDHEI_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
@@ -257,6 +272,8 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.z2_prefix = reinterpret_cast<const uint32_t*>(base + p->off_z2_prefix);
   B.total_z2_blocks = p->total_z2;
   B.strip_prefix = reinterpret_cast<const uint32_t*>(base + p->off_strip_prefix);
+  B.tile_owner = reinterpret_cast<const uint32_t*>(base + p->off_tile_owner);
+  B.strip_owner = reinterpret_cast<const uint32_t*>(base + p->off_strip_owner);
   B.total_strips = p->total_strips;
   B.n_images = n;
   B.total_tiles = p->total_tiles;

@@ -68,6 +68,8 @@ struct Batch {
   const uint32_t* chunk_prefix;   // n + 1 entries
   const uint32_t* z2_prefix;      // n + 1 entries: first K2 keystream block of each image
   const uint32_t* strip_prefix;   // n + 1 entries: first 64-row strip of each image
+  const uint32_t* tile_owner;     // total_tiles entries: image of each global tile
+  const uint32_t* strip_owner;    // total_strips entries: image of each global strip
   uint32_t total_strips;
   uint32_t total_z2_blocks;
   int n_images;

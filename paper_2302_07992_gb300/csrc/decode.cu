@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
 
   const int t = threadIdx.x;
   const uint32_t s = blockIdx.x;
-  const int img = owner_of(B.strip_prefix, B.n_images, s);
+  const int img = (int)__ldg(B.strip_owner + s);
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W;
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
   __shared__ __align__(16) uint8_t uprow[ANY_MED ? TILE + 16 : 16];   // MED: the row above P, its left corner
 
   const uint32_t g = blockIdx.x;
-  const int img = owner_of(B.tile_prefix, B.n_images, g);
+  const int img = (int)__ldg(B.tile_owner + g);
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W;
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);

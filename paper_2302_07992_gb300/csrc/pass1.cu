@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   __shared__ uint32_t zero_cnt[2][8];
 
   const uint32_t g = blockIdx.x;
-  const int img = owner_of(B.tile_prefix, B.n_images, g);
+  const int img = (int)__ldg(B.tile_owner + g);
   const ImgDesc& d = B.desc[img];
   const uint32_t t_local = g - d.tile_base;
   const int ty = (int)(t_local / d.tiles_x), tx = (int)(t_local % d.tiles_x);
