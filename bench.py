@@ -887,7 +887,7 @@ def main():
     ap.add_argument("--c3-small", type=int, default=256)
     ap.add_argument("--c3-big", type=int, default=4)
     ap.add_argument("--c4-images", type=int, default=64)
-    ap.add_argument("--e2e-chunks", type=int, default=4)
+    ap.add_argument("--e2e-chunks", type=int, default=2)
     ap.add_argument("--med", action="store_true",
                     help="the related-work MED predictor variants (EMR_MED / LMR_MED) instead of the paper's "
                          "glide; recovery runs as a tiled anti-diagonal wavefront")

@@ -144,7 +144,8 @@ class OverlappedPipeline:
     Payloads and extracted bits are packed per image to their capacity, so only the
     bytes that carry bits cross the bus."""
 
-    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda", wave_cols=None):
+    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=2, device="cuda", wave_cols=None,
+                 graphs=True):
         self.n, self.H, self.W = n, H, W
         self.dev = torch.device(device)
         N = H * W
@@ -203,6 +204,21 @@ class OverlappedPipeline:
         self.ev_comp = [torch.cuda.Event() for _ in range(nc)]
         self.ev_down = [torch.cuda.Event() for _ in range(nc)]
         self.started = False
+        # each chunk's four operations as one CUDA graph (fewer launch gaps on the GPU)
+        self.graphs = None
+        if graphs:
+            with torch.cuda.stream(self.comp):
+                for per in self.plans:
+                    for plan, op in per:
+                        plan.run(op, self.comp)          # warm the launch path outside capture
+            self.comp.synchronize()
+            self.graphs = []
+            for per in self.plans:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.comp):
+                    for plan, op in per:
+                        plan.run(op, self.comp)
+                self.graphs.append(g)
 
     def host_buffers(self):
         """Pinned host buffers of the right sizes: (pixels, payload, side) in and
@@ -247,8 +263,12 @@ class OverlappedPipeline:
             self.comp.wait_event(up_done)
             if self.started:
                 self.comp.wait_event(self.ev_down[c])         # results of the previous run are down
-            for plan, op in self.plans[c]:
-                plan.run(op, self.comp)
+            if self.graphs is not None:
+                with torch.cuda.stream(self.comp):
+                    self.graphs[c].replay()
+            else:
+                for plan, op in self.plans[c]:
+                    plan.run(op, self.comp)
             self.ev_comp[c].record(self.comp)
             with torch.cuda.stream(self.down):
                 self.down.wait_event(self.ev_comp[c])
