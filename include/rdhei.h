@@ -181,11 +181,14 @@ const char *rdhei_stage_name(int op, int stage);
 int rdhei_plan_run_stage(rdhei_plan *plan, int op, int stage, void *stream);
 int rdhei_plan_stage_active(const rdhei_plan *plan, int op, int stage);
 
-/* Tile width of the MED recovery wavefront (64, 128 = default, or 256 columns; 32 rows):
+/* Form of the MED recovery wavefront.  cols = 64, 128 (default) or 256: tiles of 32
+ * rows x cols columns, one warp each, taken in anti-diagonal order over all images;
  * narrow tiles give more tiles per anti-diagonal, wide ones fewer idle lanes in each
- * tile's diagonal ramp.  Call after rdhei_plan_create and BEFORE
- * rdhei_plan_workspace_size / rdhei_plan_upload (it changes the layout).  Returns
- * RDHEI_EINVAL for another width or an uploaded plan. */
+ * tile's diagonal ramp.  cols = 0: the row-band pipeline, one CTA of 16 warps per image,
+ * each warp a 32-row band running a few dozen steps behind the band above (shorter
+ * critical path per image, less parallelism across images).  Call after
+ * rdhei_plan_create and BEFORE rdhei_plan_workspace_size / rdhei_plan_upload (it
+ * changes the layout).  Returns RDHEI_EINVAL for another value or an uploaded plan. */
 int rdhei_plan_set_wave_cols(rdhei_plan *plan, int cols);
 
 /* ---------------------------------------------------------------------------------

@@ -60,10 +60,18 @@ static int validate_job(const rdhei_job& j) {
   return RDHEI_OK;
 }
 
-// MED recovery tiles (32 x wave_cols), ordered by anti-diagonal (ty + tx) across all
-// images, so every tile's upper and left neighbours come earlier in the list.
+// MED recovery work list.  Tile mode (wave_cols 64 / 128 / 256): tiles of 32 x wave_cols,
+// ordered by anti-diagonal (ty + tx) across all images, so every tile's upper and left
+// neighbours come earlier in the list.  Band mode (wave_cols 0): one entry per MED image.
 static int layout_wave(rdhei_plan* p) {
   const int n = (int)p->jobs.size();
+  if (p->wave_cols == 0) {
+    p->wave_list.clear();
+    for (int i = 0; i < n; i++)
+      if (p->desc[i].med) p->wave_list.push_back(make_uint2((uint32_t)i, 0u));
+    p->total_wave = (uint32_t)p->wave_list.size();
+    return RDHEI_OK;
+  }
   const uint32_t wc = (uint32_t)p->wave_cols;
   uint32_t maxdiag = 0;
   uint64_t wave = 0;
@@ -422,7 +430,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
 }
 
 int rdhei_plan_set_wave_cols(rdhei_plan* p, int cols) {
-  if (!p || p->ws || (cols != 64 && cols != 128 && cols != 256)) return RDHEI_EINVAL;
+  if (!p || p->ws || (cols != 0 && cols != 64 && cols != 128 && cols != 256)) return RDHEI_EINVAL;
   p->wave_cols = cols;
   if (layout_wave(p) != RDHEI_OK) return RDHEI_EINVAL;
   build_layout(p);

@@ -88,7 +88,7 @@ struct Batch {
   uint32_t* wave_flags;           // MED decode: total_wave done flags (zeroed per call)
   const uint2* wave_list;         // MED decode: (image, ty << 16 | tx) in anti-diagonal order
   uint32_t total_wave;
-  int32_t wave_cols;              // MED decode: wavefront tile width (64, 128 or 256)
+  int32_t wave_cols;              // MED decode: 0 = row-band pipeline, else tile width (64, 128, 256)
 };
 
 // MED recovery wavefront tile: 32 rows (one warp lane per row) x wave_cols columns.

@@ -162,6 +162,219 @@ __global__ void __launch_bounds__(32 * WAVE_WARPS) k_med_wave(Batch B) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Row-band pipeline (wave_cols = 0).  One CTA per image at a time (ticket dispenser
+// over the MED images), BAND_WARPS warps; warp w recovers the 32-row bands w,
+// w + BAND_WARPS, ...  Lane r owns row r of its band and step s recovers column s - r,
+// so a band is one continuous wavefront of W + 31 steps.  A band only needs the last
+// row of the band above, so it runs a few dozen steps behind it instead of a whole
+// tile behind: the image's critical path is about W + 48 * bands steps.
+//   * Inside a round the edge row goes from warp w to warp w + 1 through a shared ring
+//     of RING bytes, with monotonic produced / consumed counters checked every
+//     BAND_G steps (the producer may run at most RING columns ahead).
+//   * The first band of the next round reads the previous round's last band from the
+//     image itself, published per stored 64-column chunk (no back-pressure, so the
+//     wait graph has no cycle).
+//   * Pixels, labels (and, for the first band of a round, the row above) are staged in
+//     shared memory by 64-column chunks, double-buffered; a chunk is written back and
+//     its buffer refilled once every lane has passed it.
+// Every wait is bounded by WAIT_LIMIT_NS, after which the error word is set and the
+// warp carries on (outputs invalid, no hang).
+// ---------------------------------------------------------------------------------
+constexpr int BAND_WARPS = 16;
+constexpr int BAND_CH = 64;            // staged columns per chunk
+constexpr int BAND_G = 16;             // steps between counter checks
+constexpr int RING = 256;              // edge-row ring per channel (power of two)
+constexpr int BAND_PITCH = BAND_CH + 4;   // staged row pitch: the diagonal of a step hits 32 banks
+
+struct BandSmem {
+  uint8_t px[BAND_WARPS][2][WAVE_ROWS][BAND_PITCH];   // staged pixels, recovered in place
+  uint64_t lab[BAND_WARPS][2][WAVE_ROWS];             // label words of the staged chunks
+  uint8_t up[BAND_WARPS][2][BAND_CH + 4];             // [0] = column 64k - 1, [1 + j] = column 64k + j
+  uint8_t ring[BAND_WARPS][RING];                     // edge row of warp w's band, for warp w + 1
+  volatile uint32_t produced[BAND_WARPS], consumed[BAND_WARPS];
+  volatile uint32_t wrap_stored;                      // columns of the round's last band in the image
+  uint32_t img;
+};
+
+__device__ __forceinline__ bool band_wait_ge(volatile uint32_t* v, uint32_t target, uint32_t* err) {
+  if (*v >= target) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (*v < target) {
+    if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) { set_error(err, ERR_TIMEOUT); return false; }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * BAND_WARPS, 2) k_med_band(Batch B) {
+  extern __shared__ __align__(16) uint8_t band_smem[];
+  BandSmem& S = *reinterpret_cast<BandSmem*>(band_smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S.img = atomicAdd(B.tickets + 7, 1u);
+      S.wrap_stored = 0;
+    }
+    if (threadIdx.x < BAND_WARPS) { S.produced[threadIdx.x] = 0; S.consumed[threadIdx.x] = 0; }
+    __syncthreads();
+    if (S.img >= B.total_wave) return;
+    const ImgDesc& d = B.desc[B.wave_list[S.img].x];
+    const int H = d.H, W = d.W;
+    const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+    const int b = d.b > 0 ? d.b : info->b;
+    const bool lmr = d.variant == RDHEI_LMR;
+    const uint32_t FM = lmr ? (((1u << (b - 1)) - 1u) << (8 - b)) : ((0xFFu << (8 - b)) & 0xFFu);
+    uint8_t* img = d.dst;
+    const int nb = (H + WAVE_ROWS - 1) / WAVE_ROWS;
+    const int nch = (W + BAND_CH - 1) / BAND_CH;
+    const bool words = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(img) & 3) == 0;
+
+    for (int band = warp; band < nb; band += BAND_WARPS) {
+      const int y0 = band * WAVE_ROWS, rows = min(WAVE_ROWS, H - y0);
+      const uint32_t k = (uint32_t)(band / BAND_WARPS);             // round
+      const uint32_t seq0 = k * (uint32_t)W;                        // channel sequence base
+      const bool wrap_in = band > 0 && warp == 0;                   // upper band: previous round
+      const bool ring_in = band > 0 && warp > 0;
+      const bool ring_out = band + 1 < nb && warp + 1 < BAND_WARPS;
+      const bool wrap_out = band + 1 < nb && warp + 1 == BAND_WARPS;
+
+      // stage chunk q into buffer q & 1: pixels, label words and (first band of a
+      // round) the row above, once the previous round's last band has stored it
+      auto stage = [&](int q) {
+        const int c0 = q * BAND_CH, cols = min(BAND_CH, W - c0), bi = q & 1;
+        if (wrap_in) {
+          band_wait_ge(&S.wrap_stored, (k - 1) * (uint32_t)W + (uint32_t)(c0 + cols), B.err);
+          __threadfence_block();
+          const uint8_t* ur = img + (size_t)(y0 - 1) * W;
+          for (int j = lane; j < cols; j += 32) S.up[warp][bi][1 + j] = __ldcg(ur + c0 + j);
+          if (lane == 0) S.up[warp][bi][0] = c0 > 0 ? __ldcg(ur + c0 - 1) : (uint8_t)0;
+        }
+        if (words) {
+          for (int i = lane; i < rows * (BAND_CH / 4); i += 32) {
+            const int r = i / (BAND_CH / 4), c = 4 * (i % (BAND_CH / 4));
+            if (c < cols)
+              *reinterpret_cast<uint32_t*>(&S.px[warp][bi][r][c]) =
+                  *reinterpret_cast<const uint32_t*>(img + (size_t)(y0 + r) * W + c0 + c);
+          }
+        } else {
+          for (int i = lane; i < rows * BAND_CH; i += 32) {
+            const int r = i / BAND_CH, c = i % BAND_CH;
+            if (c < cols) S.px[warp][bi][r][c] = img[(size_t)(y0 + r) * W + c0 + c];
+          }
+        }
+        if (lane < rows) S.lab[warp][bi][lane] = lab_row64(B, d, y0 + lane, q);
+      };
+      // write chunk q back to the image
+      auto store = [&](int q) {
+        const int c0 = q * BAND_CH, cols = min(BAND_CH, W - c0), bi = q & 1;
+        if (words) {
+          for (int i = lane; i < rows * (BAND_CH / 4); i += 32) {
+            const int r = i / (BAND_CH / 4), c = 4 * (i % (BAND_CH / 4));
+            if (c < cols)
+              *reinterpret_cast<uint32_t*>(img + (size_t)(y0 + r) * W + c0 + c) =
+                  *reinterpret_cast<const uint32_t*>(&S.px[warp][bi][r][c]);
+          }
+        } else {
+          for (int i = lane; i < rows * BAND_CH; i += 32) {
+            const int r = i / BAND_CH, c = i % BAND_CH;
+            if (c < cols) img[(size_t)(y0 + r) * W + c0 + c] = S.px[warp][bi][r][c];
+          }
+        }
+      };
+      stage(0);
+      if (nch > 1) stage(1);
+      __syncwarp();
+
+      const int y = y0 + lane;
+      const int T = W + WAVE_ROWS - 1;
+      uint32_t o1 = 0, o0 = 0;                  // my last two results
+      uint64_t lb = 0;
+      int next_store = 0;
+      for (int s0 = 0; s0 < T; s0 += BAND_G) {
+        // the band above must have produced the columns lane 0 reads in this block; the
+        // band below must have consumed the ring slots lane 31 overwrites
+        if (ring_in) band_wait_ge(&S.produced[warp - 1], seq0 + (uint32_t)min(s0 + BAND_G, W), B.err);
+        if (ring_out) {
+          // slot (seq0 + c) & (RING - 1) last held column seq0 + c - RING of this channel,
+          // possibly of the previous round's band
+          const int last = min(s0 - (WAVE_ROWS - 1) + BAND_G, W);
+          const int64_t need = (int64_t)seq0 + last - RING;
+          if (last > 0 && need > 0) band_wait_ge(&S.consumed[warp], (uint32_t)need, B.err);
+        }
+        __syncwarp();
+        __threadfence_block();
+#pragma unroll 4
+        for (int j = 0; j < BAND_G; j++) {
+          const int s = s0 + j;
+          const uint32_t bu = __shfl_up_sync(0xffffffffu, o1, 1);   // lane r-1: pixel (r-1, c)
+          const uint32_t cu = __shfl_up_sync(0xffffffffu, o0, 1);   // lane r-1: pixel (r-1, c-1)
+          const int c = s - lane;
+          o0 = o1;
+          if (lane < rows && c >= 0 && c < W) {
+            const int bi = (c >> 6) & 1, cc = c & (BAND_CH - 1);
+            if (cc == 0) lb = S.lab[warp][bi][lane];
+            const uint32_t D = S.px[warp][bi][lane][cc];
+            uint32_t out = D;
+            if (!(lb & 1ull)) {
+              const uint32_t A = o1;
+              uint32_t Bv, C;
+              if (lane > 0) { Bv = bu; C = cu; }
+              else if (ring_in) {
+                Bv = S.ring[warp - 1][(seq0 + (uint32_t)c) & (RING - 1)];
+                C = S.ring[warp - 1][(seq0 + (uint32_t)c - 1u) & (RING - 1)];
+              } else if (wrap_in) {
+                Bv = S.up[warp][bi][1 + cc];
+                C = S.up[warp][bi][cc];
+              } else { Bv = 0; C = 0; }
+              uint32_t pred;
+              if (y == 0) pred = lmr ? A : (A & 0xFEu);                 // row 0: from the left
+              else if (c == 0) pred = lmr ? Bv : (Bv & 0xFEu);          // column 0: from above
+              else {
+                const uint32_t a = lmr ? A : A >> 1, bb = lmr ? Bv : Bv >> 1, cc2 = lmr ? C : C >> 1;
+                const uint32_t mx = max(a, bb), mn = min(a, bb);
+                const uint32_t m = cc2 >= mx ? mn : cc2 <= mn ? mx : a + bb - cc2;
+                pred = lmr ? m : m << 1;
+              }
+              out = (pred & FM) | (D & ~FM & 0xFFu);
+            }
+            lb >>= 1;
+            S.px[warp][bi][lane][cc] = (uint8_t)out;
+            if (ring_out && lane == WAVE_ROWS - 1) S.ring[warp][(seq0 + (uint32_t)c) & (RING - 1)] = (uint8_t)out;
+            o1 = out;
+          }
+        }
+        __syncwarp();
+        __threadfence_block();
+        const int s_end = min(s0 + BAND_G, T);
+        if (lane == 0) {
+          if (ring_out) S.produced[warp] = seq0 + (uint32_t)max(0, min(s_end - (WAVE_ROWS - 1), W));
+          if (ring_in) S.consumed[warp - 1] = seq0 + (uint32_t)min(s_end, W);
+        }
+        // chunks every lane has passed: write back, refill the buffer with chunk + 2
+        const int cdone = min(s_end - rows, W - 1);   // last column finished by every row
+        while (next_store < nch && min((next_store + 1) * BAND_CH, W) - 1 <= cdone) {
+          store(next_store);
+          __syncwarp();
+          if (wrap_out) {
+            __threadfence_block();
+            if (lane == 0) S.wrap_stored = seq0 + (uint32_t)min((next_store + 1) * BAND_CH, W);
+          }
+          if (next_store + 2 < nch) stage(next_store + 2);
+          __syncwarp();
+          next_store++;
+        }
+      }
+      if (lane == 0) {
+        if (ring_out) S.produced[warp] = seq0 + (uint32_t)W;
+        if (ring_in) S.consumed[warp - 1] = seq0 + (uint32_t)W;
+      }
+    }
+    __threadfence();                             // the image's pixels are out before the next image
+  }
+}
+
 template <int WCOLS>
 static void launch_wave_cols(const Batch& B, cudaStream_t st) {
   int dev = 0, sms = 1, occ = 1;
@@ -176,6 +389,18 @@ static void launch_wave_cols(const Batch& B, cudaStream_t st) {
 
 void launch_med_wave(const Batch& B, cudaStream_t st) {
   if (B.total_wave == 0) return;
+  if (B.wave_cols == 0) {
+    const int smem = (int)sizeof(BandSmem);
+    cudaFuncSetAttribute(k_med_band, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 1, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_med_band, 32 * BAND_WARPS, smem);
+    uint32_t grid = (uint32_t)(sms * (occ > 0 ? occ : 1));
+    if (grid > B.total_wave) grid = B.total_wave;
+    k_med_band<<<grid, 32 * BAND_WARPS, smem, st>>>(B);
+    return;
+  }
   if (B.wave_cols == 64) launch_wave_cols<64>(B, st);
   else if (B.wave_cols == 256) launch_wave_cols<256>(B, st);
   else launch_wave_cols<128>(B, st);

@@ -1,7 +1,7 @@
 """Autotuner for the launch shapes that the kernels leave open, with a cache.
 
-What is tuned: the tile width of the MED recovery wavefront (64, 128 or 256 columns
-of 32 rows).  The paper's own path has no free tile shape: its 64 x 64 tiles follow
+What is tuned: the form of the MED recovery wavefront -- the row-band pipeline (0) or
+tiles of 32 rows and 64, 128 or 256 columns.  The paper's own path has no free tile shape: its 64 x 64 tiles follow
 from the rotation's per-bit closed form (levels 1..6 inside a tile).
 
 How: for a batch of decode jobs, each candidate width gets its own plan; the first
@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 from . import rdhei as rd
 
-WAVE_WIDTHS = (64, 128, 256)
+WAVE_WIDTHS = (0, 64, 128, 256)          # 0: row-band pipeline
 _CACHE = os.path.join(_build.OUT, "tune_cache.json")
 
 

@@ -91,11 +91,13 @@ def test_mixed_batch_in_one_plan(rd):
     assert dec_plan.status() == 0
 
 
-@pytest.mark.parametrize("cols", [64, 128, 256])
-def test_wave_widths_agree(rd, cols):
-    """Every wavefront tile width recovers the oracle's image; the wavefront stage can
-    be rerun on restaged pixels (it clears its own flags and ticket)."""
-    H, W = 200, 530
+@pytest.mark.parametrize("cols", [0, 64, 128, 256])
+@pytest.mark.parametrize("shape", [(200, 530), (1100, 70), (37, 1000), (600, 333)])
+def test_wave_widths_agree(rd, cols, shape):
+    """The row-band pipeline (0) and every tile width recover the oracle's image; the
+    wavefront stage can be rerun on restaged pixels (it clears its own flags and
+    ticket).  1100 rows = 35 bands: three rounds of the 16-warp band pipeline."""
+    H, W = shape
     img = synth.synth_image(H, W, 61)
     for variant in (oracle.EMR_MED, oracle.LMR_MED):
         k = synth.keys(61)
