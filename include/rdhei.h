@@ -56,7 +56,9 @@ enum rdhei_status {
     RDHEI_ECAPACITY = 2,  /* payload longer than the capacity: only the capacity is embedded */
     RDHEI_ECUDA = 3,      /* a CUDA runtime call failed */
     RDHEI_ETIMEOUT = 4,   /* a bounded device-side wait gave up; outputs are invalid */
-    RDHEI_ESPACE = 5      /* workspace too small */
+    RDHEI_ESPACE = 5,     /* workspace too small */
+    RDHEI_EBOUNDS = 6     /* checked build (-DRDHEI_CHECK) only: a device index check failed
+                             and the access was skipped; outputs are invalid */
 };
 
 /* RDHEI_EMR / RDHEI_LMR are the paper's methods: labels compare a pixel's top b bits
@@ -332,6 +334,15 @@ size_t rdhei_side_unpack_job_size(void);
 #define RDHEI_NOALLOC_MAX_PIXELS (1u << 24)
 int rdhei_extract_noalloc(const rdhei_job *job, void *stream);
 
+/* Failure-detection self-test of the bounded device-side wait that the MED
+ * wavefront's tiles use on their neighbours' done flags: one warp waits until the
+ * device word *flag is non-zero or limit_ns nanoseconds of %globaltimer have passed
+ * (clamped to the library's 2 s bound), then writes RDHEI_OK or RDHEI_ETIMEOUT to the
+ * device word *status and returns; the context stays usable either way.  flag and
+ * status: device pointers, 4-byte aligned.  Asynchronous on `stream`.  Returns
+ * RDHEI_EINVAL for null or misaligned pointers, RDHEI_ECUDA for a failed launch. */
+int rdhei_wait_selftest(const uint32_t *flag, uint64_t limit_ns, int32_t *status, void *stream);
+
 /* Workspace-wide device error word of the most recent call on this workspace
  * (synchronises the stream).  0 = no error, else an rdhei_status code. */
 int rdhei_workspace_status(void *ws, void *stream, int32_t *code);
@@ -344,6 +355,14 @@ size_t rdhei_stats_job_size(void);
 
 /* Library version and build target, e.g. "rdhei 0.1 sm_103a". */
 const char *rdhei_version(void);
+
+/* Build options of this library: RDHEI_BUILD_CHECKED is set in the checked build
+ * (compiled with -DRDHEI_CHECK), whose kernels test their data-dependent indexes
+ * (tile-map targets, slot-buffer and output-word positions) before each access; a
+ * failing test skips the access and the call returns RDHEI_EBOUNDS.  The normal build
+ * returns 0 and carries no checks. */
+#define RDHEI_BUILD_CHECKED 1
+int rdhei_build_flags(void);
 
 #ifdef __cplusplus
 }

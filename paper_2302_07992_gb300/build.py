@@ -2,6 +2,10 @@
 
 Plain nvcc, one ``-gencode`` (compute_103a / sm_103a), translation units compiled in
 parallel, then linked with ``-shared``.  Nothing is installed outside this folder.
+
+``build(checked=True)`` makes the checked library ``_build/librdhei_check.so``
+(``-DRDHEI_CHECK``: device index checks that report ``RDHEI_EBOUNDS`` instead of
+touching memory out of range); ``rdhei`` loads it when ``RDHEI_CHECKED=1``.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librdhei.so")
+LIB_CHECKED = os.path.join(OUT, "librdhei_check.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -34,24 +39,28 @@ def _deps():
     return _sources() + glob.glob(os.path.join(SRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "rdhei.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    objdir = os.path.join(OUT, "check") if checked else OUT
+    os.makedirs(objdir, exist_ok=True)
     nv = nvcc()
     flags = ["-gencode", GENCODE, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
+    flags += ["-DRDHEI_CHECK"] if checked else []
     flags += list(extra or [])
     objs = []
 
     def one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nv] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,14 +72,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             objs.append(obj)
             if verbose:
                 sys.stderr.write(log)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nv, "-shared", "-gencode", GENCODE, "-cudart", "static", "-o", tmp] + objs
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = [nv, "-shared", "-gencode", GENCODE, "-cudart", "static", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

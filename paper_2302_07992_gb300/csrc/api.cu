@@ -374,6 +374,7 @@ const char* rdhei_stage_name(int op, int stage) {
 int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
   if (!p || !p->ws) return RDHEI_EINVAL;
   if (stage < 0 || stage >= rdhei_plan_stage_count(op)) return RDHEI_EINVAL;
+  NvtxRange range(rdhei_stage_name(op, stage));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Batch& B = p->batch;
   if (stage == 0) {
@@ -443,9 +444,21 @@ int rdhei_plan_stage_active(const rdhei_plan* p, int op, int stage) {
   return 1;
 }
 
+static const char* op_range_name(int op) {
+  switch (op) {
+    case RDHEI_OP_LABEL_ENCRYPT: return "rdhei_label_encrypt";
+    case RDHEI_OP_EMBED: return "rdhei_embed";
+    case RDHEI_OP_EXTRACT: return "rdhei_extract";
+    case RDHEI_OP_DECRYPT_RECOVER: return "rdhei_decrypt_recover";
+    case RDHEI_OP_LMR_SET_SIDE: return "rdhei_lmr_set_side";
+  }
+  return "rdhei_plan_run";
+}
+
 int rdhei_plan_run(rdhei_plan* p, int op, void* stream) {
   const int n = rdhei_plan_stage_count(op);
   if (n == 0) return RDHEI_EINVAL;
+  NvtxRange range(op_range_name(op));
   for (int s = 0; s < n; s++) {
     int rc = rdhei_plan_run_stage(p, op, s, stream);
     if (rc) return rc;
@@ -503,5 +516,13 @@ size_t rdhei_job_size(void) { return sizeof(rdhei_job); }
 size_t rdhei_info_size(void) { return sizeof(rdhei_info); }
 
 const char* rdhei_version(void) { return "rdhei 0.1 sm_103a"; }
+
+int rdhei_build_flags(void) {
+#ifdef RDHEI_CHECK
+  return RDHEI_BUILD_CHECKED;
+#else
+  return 0;
+#endif
+}
 
 }  // extern "C"

@@ -12,8 +12,18 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace rdhei {
+
+// Host-side NVTX range for the lifetime of a scope (one ABI call or one stage); with
+// no profiler attached a push / pop is a check of an unset function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int TILE = 64;                 // tile side (pixels)
 constexpr int TILE_PX = TILE * TILE;
@@ -107,6 +117,7 @@ __device__ __forceinline__ uint32_t med4(uint32_t A, uint32_t Bv, uint32_t C) {
 // Error codes shared with rdhei.h.
 constexpr int ERR_CAPACITY = 2;
 constexpr int ERR_TIMEOUT = 4;
+constexpr int ERR_BOUNDS = 6;
 
 // ------------------------------------------------------------------------------------
 // ChaCha20 block function (RFC 8439 Sec. 2.3), 20 rounds, written for the GPU: the 16
@@ -178,6 +189,19 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 }
 
 __device__ __forceinline__ void set_error(uint32_t* err, int code) { atomicCAS(err, 0u, (uint32_t)code); }
+
+// Index checks of the checked build (-DRDHEI_CHECK, a stand-in for a memory checker):
+// a failing check records ERR_BOUNDS in the workspace error word and the caller skips
+// the access.  The normal build compiles every check to `true`.
+#ifdef RDHEI_CHECK
+__device__ __forceinline__ bool idx_ok(uint32_t* err, bool cond) {
+  if (!cond) set_error(err, ERR_BOUNDS);
+  return cond;
+}
+#define RDHEI_IDX_OK(err, cond) ::rdhei::idx_ok((err), (cond))
+#else
+#define RDHEI_IDX_OK(err, cond) true
+#endif
 
 // Image index owning global tile / chunk `g` (binary search in a prefix array).
 __device__ __forceinline__ int owner_of(const uint32_t* prefix, int n, uint32_t g) {

@@ -48,8 +48,9 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
     const TileMap tm = B.tilemap[g];
     nU = tm.dec_shi;
     const uint32_t Q = tm.dec_dst;
+    const bool q_ok = RDHEI_IDX_OK(B.err, Q < tiles_x * d.tiles_y);
     const int qy = (int)(Q / tiles_x) * TILE + row, qx = (int)(Q % tiles_x) * TILE + 16 * quarter;
-    int valid = (qy < H) ? min(16, W - qx) : 0;
+    int valid = (q_ok && qy < H) ? min(16, W - qx) : 0;
     if (valid < 0) valid = 0;
     const uint8_t* sp = d.stash + (size_t)qy * W + qx;
     if (valid == 16 && ((reinterpret_cast<uintptr_t>(sp) & 15) == 0)) {
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
       }
     }
     const uint16_t* ap = reinterpret_cast<const uint16_t*>(B.aux + (size_t)(d.tile_base + Q) * AUX_BYTES);
-    na = ap[row * 4 + quarter];
+    na = q_ok ? ap[row * 4 + quarter] : 0u;
   };
   fetch(0);
 

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
       qx = (qx & ~(1u << k)) | ((qb & 1u) << k);
     }
     const uint32_t q = qy * d.tiles_x + qx;
+    if (!RDHEI_IDX_OK(B.err, q < ntiles)) continue;
     const uint8_t shi = (uint8_t)(S & 3u);           // S_6
     B.tilemap[d.tile_base + t].dec_dst = q;
     B.tilemap[d.tile_base + t].dec_shi = shi;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256) k_enc_pass2(Batch B) {
   const uint32_t Q = g - d.tile_base;
   const TileMap tm = B.tilemap[g];
   const uint32_t P = tm.enc_src, U = tm.enc_shi;
+  if (!RDHEI_IDX_OK(B.err, P < d.tiles_x * d.tiles_y)) return;   // uniform over the CTA
   const int qy0 = (int)(Q / d.tiles_x) * TILE, qx0 = (int)(Q % d.tiles_x) * TILE;
   const int py0 = (int)(P / d.tiles_x) * TILE, px0 = (int)(P % d.tiles_x) * TILE;
   const int t = threadIdx.x;

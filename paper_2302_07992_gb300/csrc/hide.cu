@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
     if (!EXTRACT) {
       const uint64_t end = umin64(G + T, d.nbits);
       nw = end > G ? (uint32_t)(((end - 1) >> 5) - w_lo + 1) : 0u;
+      if (!RDHEI_IDX_OK(B.err, nw == 0 || (nw < SBUF_WORDS && w_lo + nw <= ((d.nbits + 31) >> 5)))) nw = 0;
       const uint32_t* e = reinterpret_cast<const uint32_t*>(d.ebuf) + w_lo;
 #pragma unroll
       for (int i = 0; i < EW; i++) {
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
         for (int i = 0; i < 8; i++) {
           const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
           const uint32_t nb = (uint32_t)__popc(zw) * slots;         // <= 28 bits
-          if (nb && k < d.nbits) {
+          if (nb && k < d.nbits && RDHEI_IDX_OK(B.err, ((k - base) >> 5) + 1 < SBUF_WORDS)) {
             const uint32_t avail = (uint32_t)umin64(nb, d.nbits - k);
             const uint32_t E = get_bits(sbuf, (uint32_t)(k - base), avail) << (32 - avail);   // left-aligned
             const uint32_t rs = 32 - slots;
@@ -360,11 +361,12 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
           nacc += nb;
           if (nacc >= 32) {
             nacc -= 32;
-            or_bits(sbuf, o, (uint32_t)(acc >> nacc), 32);
+            if (RDHEI_IDX_OK(B.err, (o >> 5) + 1 < SBUF_WORDS)) or_bits(sbuf, o, (uint32_t)(acc >> nacc), 32);
             o += 32;
           }
         }
-        if (nacc) or_bits(sbuf, o, (uint32_t)acc & ((1u << nacc) - 1u), nacc);
+        if (nacc && RDHEI_IDX_OK(B.err, (o >> 5) + 1 < SBUF_WORDS))
+          or_bits(sbuf, o, (uint32_t)acc & ((1u << nacc) - 1u), nacc);
       }
       __syncthreads();
       // words of [G, min(G + T, E)), E = bits the receiver asked for and the image holds
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
         for (uint64_t w = w_lo + t; w <= w_hi; w += HIDE_THREADS) {
           const uint64_t b0 = 32 * w;
           const uint64_t lo = b0 > G ? b0 : G, hi = b0 + 32 < end ? b0 + 32 : end;   // my bits of word w
+          if (!RDHEI_IDX_OK(B.err, w < ((d.max_bits + 31) >> 5) && ((lo - G) >> 5) + 1 < SBUF_WORDS)) continue;
           uint32_t raw = get_bits(sbuf, (uint32_t)(lo - G), (uint32_t)(hi - lo));
           raw <<= (uint32_t)(b0 + 32 - hi);
           if (lo == b0 && hi == b0 + 32) out[w] = bswap32(raw);

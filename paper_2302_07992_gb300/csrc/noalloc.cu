@@ -55,6 +55,7 @@ uint32_t le32(const uint8_t* p) {
 
 extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   if (!job) return RDHEI_EINVAL;
+  NvtxRange range("rdhei_extract_noalloc");
   const rdhei_job& j = *job;
   if (j.H < 1 || j.W < 1 || (j.variant < RDHEI_EMR || j.variant > RDHEI_LMR_MED)) return RDHEI_EINVAL;
   const uint64_t N = (uint64_t)j.H * (uint64_t)j.W;

@@ -269,10 +269,12 @@ extern "C" int rdhei_bilevel_decode(const uint8_t* in, size_t len, int H, int W,
 }
 
 extern "C" int rdhei_lmr_side_pack(rdhei_side_pack_job* jobs, int n, int threads) {
+  rdhei::NvtxRange range("rdhei_lmr_side_pack");
   return run_pool(jobs, n, threads, pack_one);
 }
 
 extern "C" int rdhei_lmr_side_unpack(rdhei_side_unpack_job* jobs, int n, int threads) {
+  rdhei::NvtxRange range("rdhei_lmr_side_unpack");
   return run_pool(jobs, n, threads, unpack_one);
 }
 

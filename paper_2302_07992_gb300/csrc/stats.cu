@@ -595,6 +595,7 @@ extern "C" int rdhei_stats_plan_run_stage(rdhei_stats_plan* p, int stage, void* 
 }
 
 extern "C" int rdhei_stats_plan_run(rdhei_stats_plan* p, void* stream) {
+  NvtxRange range("rdhei_image_stats");
   int rc = rdhei_stats_plan_run_stage(p, 0, stream);
   return rc ? rc : rdhei_stats_plan_run_stage(p, 1, stream);
 }

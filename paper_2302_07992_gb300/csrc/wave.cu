@@ -19,13 +19,20 @@
 namespace rdhei {
 
 constexpr int WAVE_WARPS = 4;
-// spin (bounded by WAIT_LIMIT_NS from t0) until a tile's done flag is set
-__device__ __forceinline__ bool wait_flag(const uint32_t* f, uint64_t t0) {
+// spin (bounded by `limit` ns of %globaltimer from t0) until a tile's done flag is set
+__device__ __forceinline__ bool wait_flag(const uint32_t* f, uint64_t t0, uint64_t limit = WAIT_LIMIT_NS) {
   while (ld_acquire_u32(f) == 0u) {
-    if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) return false;
+    if (globaltimer_ns() - t0 > limit) return false;
     __nanosleep(64);
   }
   return true;
+}
+
+// Self-test of the bounded wait: one warp waits on *flag exactly as a wavefront tile
+// waits on a neighbour, then reports OK or ETIMEOUT.
+__global__ void k_wait_selftest(const uint32_t* flag, uint64_t limit, int32_t* status) {
+  const bool ok = wait_flag(flag, globaltimer_ns(), limit);
+  if (threadIdx.x == 0) *status = ok ? 0 : ERR_TIMEOUT;
 }
 
 // labels of 64 pixels of one image row, from the tile-major de-rotated label plane
@@ -407,3 +414,11 @@ void launch_med_wave(const Batch& B, cudaStream_t st) {
 }
 
 }  // namespace rdhei
+
+extern "C" int rdhei_wait_selftest(const uint32_t* flag, uint64_t limit_ns, int32_t* status, void* stream) {
+  if (!flag || !status || (reinterpret_cast<uintptr_t>(flag) & 3) || (reinterpret_cast<uintptr_t>(status) & 3))
+    return RDHEI_EINVAL;
+  if (limit_ns > rdhei::WAIT_LIMIT_NS) limit_ns = rdhei::WAIT_LIMIT_NS;
+  rdhei::k_wait_selftest<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(flag, limit_ns, status);
+  return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
+}

@@ -19,13 +19,17 @@ EMR, LMR = 0, 1
 # the related-work variants: MED (LOCO-I) prediction instead of the paper's glide
 EMR_MED, LMR_MED = 2, 3
 OP_LABEL_ENCRYPT, OP_EMBED, OP_EXTRACT, OP_DECRYPT_RECOVER, OP_LMR_SET_SIDE = 0, 1, 2, 3, 4
-STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE"}
-RDHEI_OK, RDHEI_EINVAL, RDHEI_ECAPACITY, RDHEI_ECUDA, RDHEI_ETIMEOUT, RDHEI_ESPACE = range(6)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE", 6: "EBOUNDS"}
+RDHEI_OK, RDHEI_EINVAL, RDHEI_ECAPACITY, RDHEI_ECUDA, RDHEI_ETIMEOUT, RDHEI_ESPACE, RDHEI_EBOUNDS = range(7)
+RDHEI_BUILD_CHECKED = 1
 
-if not os.path.exists(_build.LIB):
-    raise ImportError(f"{_build.LIB} is missing: build it with `python -m paper_2302_07992_gb300.build` "
-                      "(or __graft_entry__.build()); there is no CPU fallback")
-_lib = ctypes.CDLL(_build.LIB)
+# RDHEI_CHECKED=1 selects the checked build (device index checks, RDHEI_EBOUNDS)
+LIBRARY = _build.LIB_CHECKED if os.environ.get("RDHEI_CHECKED", "0") == "1" else _build.LIB
+if not os.path.exists(LIBRARY):
+    raise ImportError(f"{LIBRARY} is missing: build it with `python -m paper_2302_07992_gb300.build` "
+                      "(add --checked for the checked build, or __graft_entry__.build()); "
+                      "there is no CPU fallback")
+_lib = ctypes.CDLL(LIBRARY)
 
 
 class Job(ctypes.Structure):
@@ -81,6 +85,10 @@ _lib.rdhei_workspace_status.restype = ctypes.c_int
 _lib.rdhei_job_size.restype = ctypes.c_size_t
 _lib.rdhei_info_size.restype = ctypes.c_size_t
 _lib.rdhei_version.restype = ctypes.c_char_p
+_lib.rdhei_build_flags.argtypes = []
+_lib.rdhei_build_flags.restype = ctypes.c_int
+_lib.rdhei_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rdhei_wait_selftest.restype = ctypes.c_int
 
 assert _lib.rdhei_job_size() == ctypes.sizeof(Job), "rdhei_job layout mismatch"
 assert _lib.rdhei_info_size() == ctypes.sizeof(Info), "rdhei_info layout mismatch"
@@ -97,6 +105,21 @@ def _check(rc: int, what: str):
 
 def version() -> str:
     return _lib.rdhei_version().decode()
+
+
+def wait_selftest(flag: torch.Tensor, limit_ns: int, stream=None) -> int:
+    """Bounded-wait self-test: waits on the device word flag[0] for at most limit_ns
+    and returns the status the kernel wrote (RDHEI_OK or RDHEI_ETIMEOUT)."""
+    assert flag.is_cuda and flag.dtype in (torch.int32, torch.uint32) and flag.numel() >= 1
+    status = torch.full((1,), -1, dtype=torch.int32, device=flag.device)
+    _check(_lib.rdhei_wait_selftest(ctypes.c_void_p(flag.data_ptr()), int(limit_ns),
+                                    ctypes.c_void_p(status.data_ptr()), _stream(stream)), "rdhei_wait_selftest")
+    return int(status.item())
+
+
+def checked() -> bool:
+    """True when the loaded library is the checked build (device index checks)."""
+    return bool(_lib.rdhei_build_flags() & RDHEI_BUILD_CHECKED)
 
 
 def stages(op: int) -> list[str]:

@@ -64,3 +64,15 @@ def test_host_validation_without_gpu(lib):
     # a 512 x 512 image needs at least its stash
     hdr[0], hdr[1], hdr[2], hdr[3] = 512, 512, 0, 0
     assert lib.rdhei_workspace_size(ctypes.addressof(j), 1) >= 512 * 512
+
+
+def test_checked_build_exports_the_same_calls(lib):
+    """The checked build (-DRDHEI_CHECK) exports every declared call and says so in
+    rdhei_build_flags; the normal build carries no checks."""
+    from paper_2302_07992_gb300 import build
+    chk = ctypes.CDLL(build.build(checked=True))
+    missing = [n for n in _declared() if not hasattr(chk, n)]
+    assert not missing, missing
+    assert chk.rdhei_build_flags() == 1
+    assert lib.rdhei_build_flags() == 0
+
