@@ -178,6 +178,7 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
     std::memset(&d, 0, sizeof(d));
     d.H = j.H; d.W = j.W; d.variant = j.variant & 1; d.b = j.b;
     d.med = j.variant >> 1;
+    d.one = 1;
     d.nlev = levels_of(j.H, j.W);
     int lmin = j.rot_lmin > 0 ? j.rot_lmin : (d.variant == RDHEI_EMR ? 1 : 4);
     if (d.nlev >= 1 && lmin > d.nlev) lmin = d.nlev;

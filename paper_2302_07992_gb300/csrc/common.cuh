@@ -58,6 +58,7 @@ struct ImgDesc {
   int32_t lmin, nlev;         // effective smallest level (NO_ROTATION = none), n
   int32_t med;                // 1: MED predictor (related-work variant) instead of the glide
   uint32_t wave_base, wave_tx;   // MED recovery: first wavefront tile, wavefront tiles per row
+  uint32_t one;               // always 1 (a run-time value: see add_fma)
   uint32_t tiles_x, tiles_y, tile_base, chunk_base, nchunks;
   uint32_t k1[8], n1[3], k2[8], n2[3];
 };
@@ -121,18 +122,22 @@ constexpr int ERR_BOUNDS = 6;
 
 // ------------------------------------------------------------------------------------
 // ChaCha20 block function (RFC 8439 Sec. 2.3), 20 rounds, written for the GPU: the 16
-// state words stay in registers; rotations are funnel shifts.
+// state words stay in registers; rotations are funnel shifts.  The XORs and rotations
+// occupy the integer/logic pipe, so the additions go to the FMA pipe as integer
+// multiply-adds a * one + b, with `one` a run-time 1 (ImgDesc::one) that the compiler
+// cannot fold back into a plain add.
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t rotl32(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
+__device__ __forceinline__ uint32_t add_fma(uint32_t a, uint32_t b, uint32_t one) { return a * one + b; }
 
-#define RDHEI_QR(a, b, c, d)          \
-  a += b; d ^= a; d = rotl32(d, 16);  \
-  c += d; b ^= c; b = rotl32(b, 12);  \
-  a += b; d ^= a; d = rotl32(d, 8);   \
-  c += d; b ^= c; b = rotl32(b, 7);
+#define RDHEI_QR(a, b, c, d)                               \
+  a = add_fma(a, b, one); d ^= a; d = rotl32(d, 16);       \
+  c = add_fma(c, d, one); b ^= c; b = rotl32(b, 12);       \
+  a = add_fma(a, b, one); d ^= a; d = rotl32(d, 8);        \
+  c = add_fma(c, d, one); b ^= c; b = rotl32(b, 7);
 
 __device__ __forceinline__ void chacha20_block(const uint32_t key[8], uint32_t counter,
-                                               const uint32_t nonce[3], uint32_t o[16]) {
+                                               const uint32_t nonce[3], uint32_t o[16], uint32_t one) {
   const uint32_t c0 = 0x61707865u, c1 = 0x3320646eu, c2 = 0x79622d32u, c3 = 0x6b206574u;
   uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = c3;
   uint32_t x4 = key[0], x5 = key[1], x6 = key[2], x7 = key[3];
@@ -143,22 +148,15 @@ __device__ __forceinline__ void chacha20_block(const uint32_t key[8], uint32_t c
     RDHEI_QR(x0, x4, x8, x12) RDHEI_QR(x1, x5, x9, x13) RDHEI_QR(x2, x6, x10, x14) RDHEI_QR(x3, x7, x11, x15)
     RDHEI_QR(x0, x5, x10, x15) RDHEI_QR(x1, x6, x11, x12) RDHEI_QR(x2, x7, x8, x13) RDHEI_QR(x3, x4, x9, x14)
   }
-  o[0] = x0 + c0; o[1] = x1 + c1; o[2] = x2 + c2; o[3] = x3 + c3;
-  o[4] = x4 + key[0]; o[5] = x5 + key[1]; o[6] = x6 + key[2]; o[7] = x7 + key[3];
-  o[8] = x8 + key[4]; o[9] = x9 + key[5]; o[10] = x10 + key[6]; o[11] = x11 + key[7];
-  o[12] = x12 + counter; o[13] = x13 + nonce[0]; o[14] = x14 + nonce[1]; o[15] = x15 + nonce[2];
+  o[0] = add_fma(x0, c0, one); o[1] = add_fma(x1, c1, one); o[2] = add_fma(x2, c2, one);
+  o[3] = add_fma(x3, c3, one);
+  o[4] = add_fma(x4, key[0], one); o[5] = add_fma(x5, key[1], one); o[6] = add_fma(x6, key[2], one);
+  o[7] = add_fma(x7, key[3], one); o[8] = add_fma(x8, key[4], one); o[9] = add_fma(x9, key[5], one);
+  o[10] = add_fma(x10, key[6], one); o[11] = add_fma(x11, key[7], one);
+  o[12] = add_fma(x12, counter, one); o[13] = add_fma(x13, nonce[0], one);
+  o[14] = add_fma(x14, nonce[1], one); o[15] = add_fma(x15, nonce[2], one);
 }
 #undef RDHEI_QR
-
-// Keystream byte at absolute stream position p (slow path, one block per call).
-__device__ __forceinline__ uint32_t ks_word_at(const uint32_t key[8], const uint32_t nonce[3], uint64_t word) {
-  uint32_t o[16];
-  chacha20_block(key, (uint32_t)(word >> 4), nonce, o);
-  uint32_t r = 0;
-#pragma unroll
-  for (int i = 0; i < 16; i++) r = (i == (int)(word & 15)) ? o[i] : r;
-  return r;
-}
 
 // ------------------------------------------------------------------------------------
 // small helpers

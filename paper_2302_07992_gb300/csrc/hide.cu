@@ -132,45 +132,62 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
   return base + inc - v;
 }
 
-// Pass 1 of the payload scan: slot count of every chunk (persistent, grid-stride; the
-// next chunk's loads are in flight while the current one is reduced).
-__global__ void __launch_bounds__(HIDE_THREADS) k_count(Batch B) {
-  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(B.chunk_status);
-  // a contiguous range of chunks per CTA: the owning image only ever steps forward
-  const uint32_t per = (B.total_chunks + gridDim.x - 1) / gridDim.x;
-  uint32_t g = blockIdx.x * per;
-  const uint32_t gend = (uint32_t)umin64((uint64_t)g + per, B.total_chunks);
-  if (g >= gend) return;
-  int img = owner_of(B.chunk_prefix, B.n_images, g);
-  ChunkPx cur;
-  issue_chunk(B.desc[img], g - B.desc[img].chunk_base, t, false, cur);
-  while (g < gend) {
-    const ImgDesc& d = B.desc[img];
-    const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
-    const uint32_t gn = g + 1;
-    int imgn = img;
-    ChunkPx nxt;
-    if (gn < gend) {
-      while (gn >= __ldg(B.chunk_prefix + imgn + 1)) imgn++;
-      issue_chunk(B.desc[imgn], gn - B.desc[imgn].chunk_base, t, false, nxt);
-    }
-    uint32_t v = (uint32_t)__popc(zero_mask(d, cur)) * (uint32_t)slots_of(d, info);
-    v = __reduce_add_sync(0xffffffffu, v);
-    if (lane == 0) warp_tot[warp] = v;
-    __syncthreads();
-    if (t == 0) {
-      uint32_t T = 0;
+// Pass 1 of the payload scan: slot count of every chunk, one warp per chunk.  Chunks
+// are independent, so thousands of warps keep their reads in flight at once (no
+// block-level synchronisation, no chunk-to-chunk dependency).  EMR counts the pixels
+// whose LSB (the location-map bit) is 0, LMR the 0 bits of the packed map.
+constexpr int COUNT_WARPS = 8;
+__global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t g = blockIdx.x * COUNT_WARPS + (threadIdx.x >> 5);
+  if (g >= B.total_chunks) return;
+  const int img = owner_of(B.chunk_prefix, B.n_images, g);
+  const ImgDesc& d = B.desc[img];
+  const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+  const uint64_t N = (uint64_t)d.H * d.W;
+  const uint64_t p0 = (uint64_t)(g - d.chunk_base) * SCAN_PX;
+  const uint32_t valid = (uint32_t)umin64(SCAN_PX, N - p0);      // pixels of this chunk (>= 1)
+  uint32_t z = 0;
+  if (d.variant == RDHEI_LMR) {
+    // SCAN_PX / 32 map words, MSB-first: pixel q of a word is bit 31 - q after the byte swap
+    const uint32_t* mw = reinterpret_cast<const uint32_t*>(d.map_bits) + (p0 >> 5);
+    const uint32_t nw = (valid + 31) >> 5;
 #pragma unroll
-      for (int i = 0; i < HIDE_THREADS / 32; i++) T += warp_tot[i];
-      cnt[g] = T;
+    for (int k = 0; k < SCAN_PX / 32 / 32; k++) {
+      const uint32_t w = (uint32_t)lane + 32u * k;
+      if (w < nw) {
+        uint32_t v = ~bswap32(__ldg(mw + w));
+        const uint32_t left = valid - 32 * w;                      // pixels of this word inside the chunk
+        if (left < 32) v &= ~0u << (32 - left);
+        z += (uint32_t)__popc(v);
+      }
     }
-    __syncthreads();
-    g = gn;
-    img = imgn;
-    cur = nxt;
+  } else {
+    // pixel bytes: the 16-byte-aligned middle as uint4 (8 per lane in flight), the
+    // head and tail bytes one per lane
+    const uint8_t* src = d.src + p0;
+    const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 15);
+    const uint32_t head = min(valid, (16u - mis) & 15u);
+    const uint32_t nvec = (valid - head) >> 4;
+    const uint32_t tail0 = head + 16 * nvec;
+    if ((uint32_t)lane < head) z += (__ldg(src + lane) & 1u) ^ 1u;
+    if ((uint32_t)lane < valid - tail0) z += (__ldg(src + tail0 + lane) & 1u) ^ 1u;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    for (uint32_t k0 = 0; k0 < nvec; k0 += 32 * 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint32_t k = k0 + lane + 32 * j;
+        v[j] = k < nvec ? __ldcs(s4 + k) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        z += (uint32_t)(__popc(~v[j].x & 0x01010101u) + __popc(~v[j].y & 0x01010101u) +
+                        __popc(~v[j].z & 0x01010101u) + __popc(~v[j].w & 0x01010101u));
+    }
   }
+  z = __reduce_add_sync(0xffffffffu, z);
+  if (lane == 0) reinterpret_cast<uint32_t*>(B.chunk_status)[g] = z * (uint32_t)slots_of(d, info);
 }
 
 // Per image: exclusive prefix of the chunk counts (the bit offset at which each chunk's
@@ -412,7 +429,7 @@ __global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
   const uint64_t w0 = (uint64_t)blk * 16;
   if (w0 >= nwords) return;
   uint32_t o[16];
-  chacha20_block(d.k2, blk, d.n2, o);
+  chacha20_block(d.k2, blk, d.n2, o, d.one);
   const uint32_t* in = reinterpret_cast<const uint32_t*>(DECRYPT ? d.bits_out : d.payload);
   uint32_t* out = reinterpret_cast<uint32_t*>(DECRYPT ? d.bits_out : d.ebuf);
   const int nw = (int)umin64(16, nwords - w0);
@@ -464,7 +481,7 @@ static int persistent_grid(K kernel, uint32_t work) {
 // count + per-image offsets
 void launch_count(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
-  k_count<<<persistent_grid(k_count, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
+  k_count<<<(B.total_chunks + COUNT_WARPS - 1) / COUNT_WARPS, 32 * COUNT_WARPS, 0, st>>>(B);
   if (extract) k_offsets<true><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
   else k_offsets<false><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
 }

@@ -85,6 +85,7 @@ extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   d.max_bits = j.max_bits < 7 * N ? j.max_bits : 7 * N;
   d.info = j.info;
   d.H = j.H; d.W = j.W; d.variant = j.variant & 1; d.b = j.b;   // extraction is the same for both predictors
+  d.one = 1;
   d.nchunks = (uint32_t)((N + CHUNK_PX - 1) / CHUNK_PX);
   for (int k = 0; k < 8; k++) d.k2[k] = le32(j.k2 + 4 * k);
   for (int k = 0; k < 3; k++) d.n2[k] = le32(j.nonce2 + 4 * k);

@@ -16,14 +16,15 @@ namespace rdhei {
 
 enum { MODE_ENC = 0, MODE_DEC = 1 };
 
-// mod-4 addition of 32 packed 2-bit lanes
+// mod-4 addition of 32 packed 2-bit lanes: per lane the low bit is a0 ^ b0 and the
+// high bit a1 ^ b1 ^ (a0 & b0); the carries (a & b & low-bit mask) << 1 land on high
+// bits only, so one three-way XOR combines them
 __device__ __forceinline__ uint64_t add4(uint64_t a, uint64_t b) {
   const uint64_t L = 0x5555555555555555ull;
-  uint64_t lo = (a ^ b) & L;
-  uint64_t c = (a & b & L) << 1;
-  uint64_t hi = (a ^ b ^ c) & ~L;
-  return lo | hi;
+  return a ^ b ^ ((a & b & L) << 1);
 }
+// 4-bit field at bits 28..31 of x shifted into the bottom of acc (acc << 4 | x >> 28)
+__device__ __forceinline__ uint32_t push_nibble(uint32_t acc, uint32_t x) { return __funnelshift_l(x, acc, 4); }
 // pairwise (mod 4) sums of adjacent 2-bit lanes, compacted: 2k lanes -> k lanes
 __device__ __forceinline__ uint64_t pair4(uint64_t v) {
   const uint64_t M = 0x3333333333333333ull;
@@ -69,18 +70,18 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 #pragma unroll
     for (int i = 0; i < 16; i++) sw[i] = 0u;
   } else if (aligned || !GENERAL) {
-    chacha20_block(d.k1, (uint32_t)(base >> 6), d.n1, sw);
+    chacha20_block(d.k1, (uint32_t)(base >> 6), d.n1, sw, d.one);
   } else {
     // the row straddles two ChaCha blocks: stage both and pick the 64 bytes
     uint32_t o[16];
     const uint64_t b0 = base >> 6;
     const int off = (int)(base & 63);
     if (len > 0) {
-      chacha20_block(d.k1, (uint32_t)b0, d.n1, o);
+      chacha20_block(d.k1, (uint32_t)b0, d.n1, o, d.one);
 #pragma unroll
       for (int i = 0; i < 16; i++) ks_stage[r][i] = o[i];
       if (off + len > 64) {
-        chacha20_block(d.k1, (uint32_t)(b0 + 1), d.n1, o);
+        chacha20_block(d.k1, (uint32_t)(b0 + 1), d.n1, o, d.one);
 #pragma unroll
         for (int i = 0; i < 16; i++) ks_stage[r][16 + i] = o[i];
       } else {
@@ -222,13 +223,19 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
     uint64_t auxbits = 0;
     uint8_t* st = d.stash + base;
     if (d.variant == 0) {
+      // the LSBs of s, pixel 4i+k -> aux bit 4i+k: the multiply gathers a word's four
+      // LSBs into bits 28..31 (bit 8k -> 28+k, no overlapping partial products), and the
+      // words are shifted in from the last one down
+      uint32_t alo = 0, ahi = 0;
 #pragma unroll
-      for (int i = 0; i < 16; i++) {
-        uint32_t s = sw[i];
+      for (int i = 15; i >= 0; i--) {
+        const uint32_t s = sw[i];
         px[i] ^= s & 0xFEFEFEFEu;                       // bits 7..1 decrypted, LSB = map l
-        uint32_t nib = ((s & 0x01010101u) * 0x01020408u) >> 24;   // LSB of s, pixel 4i+k -> bit k
-        auxbits |= (uint64_t)(nib & 0xFu) << (4 * i);
+        const uint32_t x = (s & 0x01010101u) * 0x10204080u;
+        if (i >= 8) ahi = push_nibble(ahi, x);
+        else alo = push_nibble(alo, x);
       }
+      auxbits = ((uint64_t)ahi << 32) | alo;
     } else {
       const uint64_t nw = ((uint64_t)H * W + 31) >> 5;
       uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, base) : 0u;
@@ -267,13 +274,18 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   const int Ls = lmin < 1 ? 1 : (lmin > 4 ? 4 : lmin);
   uint64_t v = 0;
   if (Ls == 1) {
+    // per word: (t * 0x101) has c0+c1 in byte 1 and c2+c3 in byte 3 (each <= 6, no
+    // carries between bytes); their low two bits move to bits 28..29 and 30..31 with
+    // one more multiply (bits 8 -> 28 by 2^20, bits 24 -> 30 by 2^6), then shift in
+    uint32_t vlo = 0, vhi = 0;
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-      uint32_t t = sw[i] & 0x03030303u;
-      uint32_t u = t + (t >> 8);                           // byte0: c0+c1, byte2: c2+c3
-      uint32_t f = (u & 3u) | (((u >> 16) & 3u) << 2);
-      v |= (uint64_t)f << (4 * i);
+    for (int i = 15; i >= 0; i--) {
+      const uint32_t u = (sw[i] & 0x03030303u) * 0x0101u;
+      const uint32_t x = (u & 0x03000300u) * 0x00100040u;
+      if (i >= 8) vhi = push_nibble(vhi, x);
+      else vlo = push_nibble(vlo, x);
     }
+    v = ((uint64_t)vhi << 32) | vlo;
   } else {
     const int sh = Ls - 2;                                 // 2^sh words per lane
     uint32_t acc = 0;

@@ -33,14 +33,33 @@ def _bits(t, n):
     return t.detach().cpu().numpy()[: (n + 7) // 8]
 
 
-def _run_batch(rd, imgs, variants, seeds, side_frac=0.125):
+def _packed(imgs, fill=None, skew=0):
+    """Images laid end to end in one flat device buffer, each starting at an odd byte
+    offset (no 16-, 4- or 2-byte alignment)."""
+    sizes = [im.size for im in imgs]
+    flat = torch.zeros(sum(sizes) + 8 * len(imgs) + 16, dtype=torch.uint8, device="cuda")
+    out, off = [], 1 + skew
+    for im in imgs:
+        v = flat[off: off + im.size].view(*im.shape)
+        if fill is not None:
+            v.copy_(torch.from_numpy(np.ascontiguousarray(im)))
+        out.append(v)
+        off += im.size + 3 + 2 * (off % 3)
+    return out
+
+
+def _run_batch(rd, imgs, variants, seeds, side_frac=0.125, odd_offsets=False):
     """All four operations, one plan (one launch sequence) per operation."""
     n = len(imgs)
     P = [rd.Params(variant=v, **_keys(s)) for v, s in zip(variants, seeds)]
-    d_img = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
-    enc = [torch.empty_like(x) for x in d_img]
-    marked = [torch.empty_like(x) for x in d_img]
-    rec = [torch.empty_like(x) for x in d_img]
+    if odd_offsets:
+        d_img = _packed(imgs, fill=True)
+        enc, marked, rec = _packed(imgs, skew=2), _packed(imgs, skew=4), _packed(imgs, skew=6)
+    else:
+        d_img = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+        enc = [torch.empty_like(x) for x in d_img]
+        marked = [torch.empty_like(x) for x in d_img]
+        rec = [torch.empty_like(x) for x in d_img]
     N = [im.size for im in imgs]
     maps = [rd.bitbuf(N[i]) for i in range(n)]
     etas = [rd.bitbuf(N[i]) for i in range(n)]
@@ -108,6 +127,20 @@ def test_uneven_sizes_one_launch(rd):
     variants = [rd.EMR if i % 3 else rd.LMR for i in range(len(shapes))]
     seeds = [500 + i for i in range(len(shapes))]
     out = _run_batch(rd, imgs, variants, seeds)
+    for i in range(len(shapes)):
+        _check_against_oracle(rd, imgs, variants, seeds, out, i)
+
+
+def test_images_at_odd_byte_offsets(rd):
+    """Source, encrypted, marked and recovered images at odd byte offsets of shared
+    buffers, ragged sizes: every kernel's unaligned path against the oracle."""
+    shapes = [(100, 130), (257, 333), (64, 64), (1, 50), (333, 1000), (512, 512), (77, 8200)]
+    imgs = [synth.synth_image(H, W, 700 + i) for i, (H, W) in enumerate(shapes)]
+    variants = [rd.EMR if i % 2 == 0 else rd.LMR for i in range(len(shapes))]
+    seeds = [700 + i for i in range(len(shapes))]
+    out = _run_batch(rd, imgs, variants, seeds, odd_offsets=True)
+    ptrs = [out[k][i].data_ptr() for k in ("enc", "marked", "rec") for i in range(len(shapes))]
+    assert sum(p % 16 != 0 for p in ptrs) > len(ptrs) // 2
     for i in range(len(shapes)):
         _check_against_oracle(rd, imgs, variants, seeds, out, i)
 
