@@ -108,6 +108,30 @@ __host__ __device__ __forceinline__ uint32_t sel_compact(uint32_t z) {
   return sel;
 }
 
+// The same with the fields in reversed byte order (first field in byte 3), which is
+// the order the multiply-based field packing produces and consumes:
+//   expand_rev:  byte q <- byte 3 - rank(q) if z_q, else the zero byte;
+//   compact_rev: byte 3 - j <- byte of the j-th label-0 pixel, unused bytes zero.
+__host__ __device__ __forceinline__ uint32_t sel_expand_rev(uint32_t z) {
+  uint32_t sel = 0, r = 0;
+  for (int q = 0; q < 4; q++) {
+    const uint32_t nib = ((z >> q) & 1u) ? 3u - r++ : 4u;
+    sel |= nib << (4 * q);
+  }
+  return sel;
+}
+__host__ __device__ __forceinline__ uint32_t sel_compact_rev(uint32_t z) {
+  uint32_t sel = 0x4444u, j = 0;
+  for (int q = 0; q < 4; q++)
+    if ((z >> q) & 1u) { sel = (sel & ~(0xFu << (4 * (3 - j)))) | ((uint32_t)q << (4 * (3 - j))); j++; }
+  return sel;
+}
+// 0xFF in the bytes of the label-0 pixels of pattern z
+__host__ __device__ __forceinline__ uint32_t zero_bytes(uint32_t z) {
+  return ((z & 1u) ? 0xFFu : 0u) | ((z & 2u) ? 0xFF00u : 0u) | ((z & 4u) ? 0xFF0000u : 0u) |
+         ((z & 8u) ? 0xFF000000u : 0u);
+}
+
 // Block-wide exclusive scan of one value per thread (256 threads); returns the
 // exclusive prefix and the block total.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
@@ -245,9 +269,14 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
   constexpr int EW = (SBUF_WORDS + HIDE_THREADS - 1) / HIDE_THREADS;   // message words per thread
   __shared__ uint32_t sbuf[SBUF_WORDS];   // hider: e words (MSB-first); receiver: raw slot stream
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
-  __shared__ uint32_t s_expand[16], s_compact[16];
+  __shared__ uint32_t s_expand[16], s_expand_rev[16], s_compact_rev[16], s_zb[16];
   const int t = threadIdx.x;
-  if (t < 16) { s_expand[t] = sel_expand(t); s_compact[t] = sel_compact(t); }
+  if (t < 16) {
+    s_expand[t] = sel_expand(t);
+    s_expand_rev[t] = sel_expand_rev(t);
+    s_compact_rev[t] = sel_compact_rev(t);
+    s_zb[t] = zero_bytes(t);
+  }
   __syncthreads();
   const uint32_t* cnt = reinterpret_cast<const uint32_t*>(B.chunk_status);
   const uint32_t* off = cnt + B.total_chunks;
@@ -311,11 +340,35 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
       }
       if (t == 0) sbuf[nw] = 0u;
       __syncthreads();
-      if (zmask && G + my_off < d.nbits) {
-        // per 4-pixel word: read the word's slots at once, spread the fields to
-        // consecutive bytes, then move them to their pixels with one byte permute
+      const uint32_t FREP = (fmask << fshift) * 0x01010101u;
+      const uint32_t my_bits = (uint32_t)__popc(zmask) * slots;
+      if (zmask && G + my_off + my_bits <= d.nbits) {
+        // all my slots lie inside the message.  Per 4-pixel word: the next 32 stream
+        // bits (left-aligned) hold the word's fields f0..f3 (first field most
+        // significant); multiply-adds place f_k at bit fshift of byte 3 - k (the shifts
+        // (3 - k)(8 - s) + fshift are all >= 0), one byte permute moves field r to the
+        // r-th label-0 pixel, and a select writes the slot bits
+        const uint32_t dsh = 8u - slots;
+        const uint32_t m1 = fmask << slots, m2 = fmask << (2 * slots), m3 = fmask << (3 * slots);
+        const uint32_t u0 = 1u << fshift, u1 = u0 << dsh, u2 = u1 << dsh, u3 = u2 << dsh;
+        uint32_t idx = (uint32_t)(G + my_off - 32 * w_lo);          // stream position in sbuf
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
+          const uint32_t w = idx >> 5;
+          if (!RDHEI_IDX_OK(B.err, w + 1 < SBUF_WORDS)) break;
+          const uint32_t E = __funnelshift_l(sbuf[w + 1], sbuf[w], idx & 31);
+          const uint32_t F = E >> (32 - 4 * slots);                 // f0 .. f3, right-aligned
+          const uint32_t cons = (F & fmask) * u0 + (F & m1) * u1 + (F & m2) * u2 + (F & m3) * u3;
+          const uint32_t m = s_zb[zw] & FREP;
+          cur.px[i] = (cur.px[i] & ~m) | __byte_perm(cons, 0, s_expand_rev[zw]);
+          idx += (uint32_t)__popc(zw) * slots;
+        }
+      } else if (zmask && G + my_off < d.nbits) {
+        // the message ends inside my slots.  Per 4-pixel word: read the word's slots at
+        // once, spread the fields to consecutive bytes, then move them to their pixels
+        // with one byte permute; the slots past the message end keep their bits
         const uint64_t base = 32 * w_lo;
-        const uint32_t FREP = (fmask << fshift) * 0x01010101u;
         const uint32_t s2 = 2 * slots, s3 = 3 * slots;
         uint64_t k = G + my_off;
 #pragma unroll
@@ -357,33 +410,39 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
     } else {
       for (int i = t; i < (int)((Tb >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
       __syncthreads();
-      // gather my slots into the chunk-local stream: per 4-pixel word one byte permute
-      // packs the fields of its label-0 pixels into consecutive bytes, which are then
-      // concatenated and appended 32 bits at a time
+      // gather my slots into the chunk-local stream.  Per 4-pixel word one byte permute
+      // puts the j-th label-0 pixel in byte 3 - j; masked to the field bits, the fields
+      // are packed most-significant first by multiply-adds (byte j moves up by
+      // (4 - j)(8 - s)) and appended to a word that is stored once full: the words
+      // wholly inside my range are plain stores, the two I share with my neighbours are
+      // OR-ed (the range was cleared above)
       {
-        uint64_t acc = 0;
-        uint32_t nacc = 0, o = my_off;
         const uint32_t FREP = fmask * 0x01010101u;
-        const uint32_t s2 = 2 * slots, s3 = 3 * slots;
+        const uint32_t dsh = 8u - slots;
+        const uint32_t v3 = 1u << dsh, v2 = v3 << dsh, v1 = v2 << dsh, v0 = v1 << dsh;
+        uint32_t wi = my_off >> 5, c = my_off & 31, word = 0;
+        bool first = true;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
           const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
-          const uint32_t cnt = (uint32_t)__popc(zw);
-          const uint32_t cb = __byte_perm(cur.px[i] >> fshift, 0, s_compact[zw]) & FREP;
-          const uint32_t full = ((cb & 0xFFu) << s3) | (((cb >> 8) & 0xFFu) << s2) |
-                                (((cb >> 16) & 0xFFu) << slots) | (cb >> 24);
-          const uint32_t nb = cnt * slots;
-          const uint32_t chunk = full >> ((4 - cnt) * slots);
-          acc = (acc << nb) | chunk;
-          nacc += nb;
-          if (nacc >= 32) {
-            nacc -= 32;
-            if (RDHEI_IDX_OK(B.err, (o >> 5) + 1 < SBUF_WORDS)) or_bits(sbuf, o, (uint32_t)(acc >> nacc), 32);
-            o += 32;
+          const uint32_t nb = (uint32_t)__popc(zw) * slots;
+          const uint32_t fld = (__byte_perm(cur.px[i], 0, s_compact_rev[zw]) >> fshift) & FREP;
+          const uint32_t P = (fld & 0xFFu) * v0 + (fld & 0xFF00u) * v1 + (fld & 0xFF0000u) * v2 +
+                             (fld & 0xFF000000u) * v3;                 // nb bits, left-aligned
+          word |= P >> c;
+          c += nb;
+          if (c >= 32) {
+            if (RDHEI_IDX_OK(B.err, wi < SBUF_WORDS)) {
+              if (first) atomicOr(sbuf + wi, word);
+              else sbuf[wi] = word;
+            }
+            first = false;
+            c -= 32;
+            word = P << (nb - c);                                     // the bits that spilled over
+            wi++;
           }
         }
-        if (nacc && RDHEI_IDX_OK(B.err, (o >> 5) + 1 < SBUF_WORDS))
-          or_bits(sbuf, o, (uint32_t)acc & ((1u << nacc) - 1u), nacc);
+        if (c && RDHEI_IDX_OK(B.err, wi < SBUF_WORDS)) atomicOr(sbuf + wi, word);
       }
       __syncthreads();
       // words of [G, min(G + T, E)), E = bits the receiver asked for and the image holds

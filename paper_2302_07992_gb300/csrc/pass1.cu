@@ -199,21 +199,27 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
       }
       uint32_t dd = px[i] ^ pred;
       if (med && i == 0 && x0 == 0 && y == 0) dd |= 0xFFu;       // pixel (0, 0): never redundant
-      int valid = len - 4 * i;                    // bytes past the row end count as "differs"
-      if (valid < 4) dd |= valid <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (8 * valid));
+      if (GENERAL) {
+        // bytes past the row end count as "differs"; without GENERAL every row is 64
+        // pixels long or empty, and an empty row is zeroed below
+        const int valid = len - 4 * i;
+        if (valid < 4) dd |= valid <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (8 * valid));
+      }
+      // nz[b - 1] += 128 per pixel whose top b bits differ (the flag byte 0x80 summed by
+      // a byte dot product with 1, 1, 1, 1)
       uint32_t m = dd & 0x7F7F7F7Fu;
-      nz[0] += __popc(dd & 0x80808080u);                                   // b = 1
+      nz[0] = __dp4a(dd & 0x80808080u, 0x01010101u, nz[0]);               // b = 1
 #pragma unroll
       for (int b = 2; b <= 8; b++) {
         const uint32_t K = (0x80u - (0x100u >> b)) * 0x01010101u;            // top b bits nonzero
-        nz[b - 1] += __popc(((m + K) | dd) & 0x80808080u);
+        nz[b - 1] = __dp4a(((m + K) | dd) & 0x80808080u, 0x01010101u, nz[b - 1]);
       }
     }
     // per-row zero counts = valid pixels - nonzero ones; reduce over the CTA
 #pragma unroll
     for (int k = 0; k < 8; k++) {
       // the 64 examined bytes include the padding past the row end, all "differs"
-      uint32_t z = 64u - nz[k];
+      uint32_t z = (GENERAL || len > 0) ? 64u - (nz[k] >> 7) : 0u;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
       if (lane == 0) zero_cnt[warp][k] = z;
@@ -303,7 +309,10 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   __syncthreads();   // sub[] cleared
   const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
   const int cov_cols = W - x0;
-  for (int L = Ls; L <= 6; L++) {
+  // unrolled over the six levels: sizes, masks and store widths are constants per level
+#pragma unroll
+  for (int L = 1; L <= 6; L++) {
+    if (L < Ls) continue;                                  // entries stay 0 (sub[] cleared)
     if (L > Ls) v = pair4(v);                              // widen the columns
     if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
     else {
@@ -321,12 +330,15 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
       if (ncol > nb) ncol = nb;
       if (L < lmin || !row_cov || ncol <= 0) ang = 0;
       else if (ncol < nb) ang &= (1ull << (2 * ncol)) - 1ull;
-      const int bits = 2 * nb;                             // bits per block row
-      const int off = subtree_off(L) * 8 + br * bits;      // bit offset in sub[]
-      if (bits >= 8) {
-        for (int k = 0; k < bits / 8; k++) sub[(off >> 3) + k] = (uint8_t)(ang >> (8 * k));
-      } else {
-        atomicOr(reinterpret_cast<unsigned int*>(sub) + (off >> 5), (uint32_t)(ang & ((1u << bits) - 1)) << (off & 31));
+      // one block row = 2 nb bits at byte subtree_off(L) + br * nb / 4
+      if (L == 1) *reinterpret_cast<uint64_t*>(sub + br * 8) = ang;
+      else if (L == 2) *reinterpret_cast<uint32_t*>(sub + subtree_off(2) + br * 4) = (uint32_t)ang;
+      else if (L == 3) *reinterpret_cast<uint16_t*>(sub + subtree_off(3) + br * 2) = (uint16_t)ang;
+      else if (L == 4) sub[subtree_off(4) + br] = (uint8_t)ang;
+      else {
+        const int off = subtree_off(L) * 8 + br * 2 * nb;   // 4 or 2 bits: shared bytes, OR-ed in
+        atomicOr(reinterpret_cast<unsigned int*>(sub) + (off >> 5),
+                 (uint32_t)(ang & ((1u << (2 * nb)) - 1)) << (off & 31));
       }
     }
     if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v & 3u);  // raw tile sum for the top levels
