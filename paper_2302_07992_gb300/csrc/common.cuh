@@ -136,6 +136,9 @@ __device__ __forceinline__ uint32_t add_fma(uint32_t a, uint32_t b, uint32_t one
   a = add_fma(a, b, one); d ^= a; d = rotl32(d, 8);        \
   c = add_fma(c, d, one); b ^= c; b = rotl32(b, 7);
 
+// UNROLL: double rounds unrolled per loop iteration (10 = straight-line code; kernels
+// with much other code keep their instruction footprint small with 2).
+template <int UNROLL = 10>
 __device__ __forceinline__ void chacha20_block(const uint32_t key[8], uint32_t counter,
                                                const uint32_t nonce[3], uint32_t o[16], uint32_t one) {
   const uint32_t c0 = 0x61707865u, c1 = 0x3320646eu, c2 = 0x79622d32u, c3 = 0x6b206574u;
@@ -143,7 +146,7 @@ __device__ __forceinline__ void chacha20_block(const uint32_t key[8], uint32_t c
   uint32_t x4 = key[0], x5 = key[1], x6 = key[2], x7 = key[3];
   uint32_t x8 = key[4], x9 = key[5], x10 = key[6], x11 = key[7];
   uint32_t x12 = counter, x13 = nonce[0], x14 = nonce[1], x15 = nonce[2];
-#pragma unroll
+#pragma unroll UNROLL
   for (int i = 0; i < 10; i++) {
     RDHEI_QR(x0, x4, x8, x12) RDHEI_QR(x1, x5, x9, x13) RDHEI_QR(x2, x6, x10, x14) RDHEI_QR(x3, x7, x11, x15)
     RDHEI_QR(x0, x5, x10, x15) RDHEI_QR(x1, x6, x11, x12) RDHEI_QR(x2, x7, x8, x13) RDHEI_QR(x3, x4, x9, x14)

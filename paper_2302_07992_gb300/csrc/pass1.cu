@@ -70,18 +70,18 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 #pragma unroll
     for (int i = 0; i < 16; i++) sw[i] = 0u;
   } else if (aligned || !GENERAL) {
-    chacha20_block(d.k1, (uint32_t)(base >> 6), d.n1, sw, d.one);
+    chacha20_block<2>(d.k1, (uint32_t)(base >> 6), d.n1, sw, d.one);
   } else {
     // the row straddles two ChaCha blocks: stage both and pick the 64 bytes
     uint32_t o[16];
     const uint64_t b0 = base >> 6;
     const int off = (int)(base & 63);
     if (len > 0) {
-      chacha20_block(d.k1, (uint32_t)b0, d.n1, o, d.one);
+      chacha20_block<2>(d.k1, (uint32_t)b0, d.n1, o, d.one);
 #pragma unroll
       for (int i = 0; i < 16; i++) ks_stage[r][i] = o[i];
       if (off + len > 64) {
-        chacha20_block(d.k1, (uint32_t)(b0 + 1), d.n1, o, d.one);
+        chacha20_block<2>(d.k1, (uint32_t)(b0 + 1), d.n1, o, d.one);
 #pragma unroll
         for (int i = 0; i < 16; i++) ks_stage[r][16 + i] = o[i];
       } else {
