@@ -327,7 +327,7 @@ def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_n
     h_img.copy_(torch.from_numpy(imgs_np))
     op.pack_payloads(h_pay, [pay_np[k] for k in range(n)])
     op.pack_side(h_side, [side_np[k] for k in range(n)])
-    K = max(3, args.steps // 10)
+    K = max(10, args.steps // 4)          # enough steps that the pipeline fill and drain amortise
     for _ in range(2):
         op.run(h_img, h_pay, h_side, h_rec, h_bits)
     torch.cuda.synchronize(dev)
@@ -887,7 +887,7 @@ def main():
     ap.add_argument("--c3-small", type=int, default=256)
     ap.add_argument("--c3-big", type=int, default=4)
     ap.add_argument("--c4-images", type=int, default=64)
-    ap.add_argument("--e2e-chunks", type=int, default=2)
+    ap.add_argument("--e2e-chunks", type=int, default=4)
     ap.add_argument("--med", action="store_true",
                     help="the related-work MED predictor variants (EMR_MED / LMR_MED) instead of the paper's "
                          "glide; recovery runs as a tiled anti-diagonal wavefront")

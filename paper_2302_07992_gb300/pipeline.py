@@ -144,7 +144,7 @@ class OverlappedPipeline:
     Payloads and extracted bits are packed per image to their capacity, so only the
     bytes that carry bits cross the bus."""
 
-    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=2, device="cuda", wave_cols=None,
+    def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda", wave_cols=None,
                  graphs=True):
         self.n, self.H, self.W = n, H, W
         self.dev = torch.device(device)
