@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_offsets(Batch B) {
 // inside the chunk's range are stored, words shared with a neighbour are OR-ed (they
 // were cleared by k_offsets).
 template <bool EXTRACT>
-__global__ void __launch_bounds__(HIDE_THREADS, 4) k_scan(Batch B) {
+__global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B) {
   constexpr int EW = (SBUF_WORDS + HIDE_THREADS - 1) / HIDE_THREADS;   // message words per thread
   __shared__ uint32_t sbuf[SBUF_WORDS];   // hider: e words (MSB-first); receiver: raw slot stream
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
