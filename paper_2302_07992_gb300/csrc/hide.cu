@@ -72,12 +72,11 @@ __device__ __forceinline__ void issue_chunk(const ImgDesc& d, uint32_t c, int t,
 __device__ __forceinline__ uint32_t zero_mask(const ImgDesc& d, const ChunkPx& r) {
   uint32_t z;
   if (d.variant != RDHEI_LMR) {
+    // LSB == 0, pixel 4i+k -> bit 4i+k: the multiply gathers a word's four flags into
+    // bits 28..31 (bit 8k -> 28+k), and the words are shifted in from the last one down
     z = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t nib = (((~r.px[i]) & 0x01010101u) * 0x01020408u) >> 24;   // LSB == 0, pixel 4i+k -> bit k
-      z |= (nib & 0xFu) << (4 * i);
-    }
+    for (int i = 7; i >= 0; i--) z = __funnelshift_l(((~r.px[i]) & 0x01010101u) * 0x10204080u, z, 4);
   } else {
     z = ~r.lbits;
   }

@@ -123,10 +123,12 @@ __device__ __forceinline__ uint32_t flags16(const uint32_t w[4], int bit) {
   uint32_t v = 0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
-    uint32_t nib = ((((w[i] >> bit) & 0x01010101u) * 0x08040201u) >> 24) & 0xFu;  // px 4i at bit 3
-    v = (v << 4) | nib;
+    // the multiply gathers the word's four flags into bits 31..28 (pixel 4i at bit 31;
+    // no two partial products share a bit), then they are shifted into v
+    const uint32_t x = ((w[i] >> bit) & 0x01010101u) * 0x80402010u;
+    v = __funnelshift_l(x, v, 4);
   }
-  return v;
+  return v & 0xFFFFu;
 }
 
 // Write `n` (<= 16) MSB-first bits v16 (bit 15 first) at stream bit `pos`.  `plain`:
