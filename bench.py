@@ -499,6 +499,8 @@ def run_c5(args):
         server = sv.Server(budget_bytes=40e9, pool=pinned)
         done = server.run(reqs, realtime=True, consume=server.release)   # results are consumed on arrival
         st = sv.latency_stats(done)
+        st["batches"] = len(server.batches)
+        st["requests_per_batch"] = len(done) / max(1, len(server.batches))
         st["offered_req_s"] = rate
         st["offered_mpx_s"] = sum(r.pixels for r in reqs) / args.c5_seconds / 1e6
         results[f"x{mult:g}"] = st

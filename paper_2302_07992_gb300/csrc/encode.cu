@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
 }
 
 // ---------------------------------------------------------------------------------
-// Gather pass of the owner.  One CTA walks one row of output (rotated-domain) tiles;
-// per output tile Q:
+// Gather pass of the owner.  One CTA walks a run of output (rotated-domain) tiles in
+// one tile row: a whole row, or 1/nsplit of it when the batch has too few rows to
+// fill the GPU; per output tile Q:
 //   1. source tile P = preimage of Q; P (+ left halo column) and its subtree into
 //      shared memory -- fetched into registers while the previous tile was processed;
 //   2. location map l (Eqs. gliding1/2 in left-neighbour form) with the chosen b;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
 //      into bit 7, packed rotated maps.
 // ---------------------------------------------------------------------------------
 template <bool ANY_LMR, bool ANY_MED>
-__global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_strip(Batch B) {
+__global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint32_t nsplit) {
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
   __shared__ __align__(16) uint8_t lin[ANY_LMR ? TILE * TPITCH : 16];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_strip(Batch B) {
   __shared__ __align__(16) uint8_t uprow[ANY_MED ? TILE + 16 : 16];   // MED: the row above P, its left corner
 
   const int t = threadIdx.x;
-  const uint32_t strip = blockIdx.x;
+  const uint32_t strip = blockIdx.x / nsplit, piece = blockIdx.x % nsplit;
   const int img = (int)__ldg(B.strip_owner + strip);
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W;
@@ -126,6 +127,9 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_strip(Batch B) {
   const bool med = ANY_MED && d.med != 0;
   const uint32_t tiles_x = d.tiles_x, ntiles = tiles_x * d.tiles_y;
   const uint32_t qty = strip - __ldg(B.strip_prefix + img);       // output tile row
+  const uint32_t per = (tiles_x + nsplit - 1) / nsplit;
+  const uint32_t tx0 = piece * per, tx1 = min(tx0 + per, tiles_x);
+  if (tx0 >= tx1) return;
   const int row = t >> 2, quarter = t & 3;
   if (t < 16) selt[t] = pair_selectors(t & 3u, t >> 2);
 
@@ -159,9 +163,9 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_strip(Batch B) {
     if (t < SUBTREE_BYTES / 4)
       nsub = __ldg(reinterpret_cast<const uint32_t*>(B.subtree + (size_t)(d.tile_base + nP) * SUBTREE_BYTES) + t);
   };
-  fetch(0);
+  fetch(tx0);
 
-  for (uint32_t tx = 0; tx < tiles_x; tx++) {
+  for (uint32_t tx = tx0; tx < tx1; tx++) {
     const uint32_t P = nP, U = nU;
     const uint32_t w[4] = {nw[0], nw[1], nw[2], nw[3]};
     const int qy0 = (int)qty * TILE, qx0 = (int)tx * TILE;
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_strip(Batch B) {
         uprow[16 * quarter + k] = (uy >= 0 && x + k < W) ? __ldg(d.src + (size_t)uy * W + x + k) : (uint8_t)0;
       if (quarter == 0) uprow[TILE] = (uy >= 0 && px0 > 0) ? __ldg(d.src + (size_t)uy * W + px0 - 1) : (uint8_t)0;
     }
-    if (tx + 1 < tiles_x) fetch(tx + 1);        // in flight while this tile is processed
+    if (tx + 1 < tx1) fetch(tx + 1);            // in flight while this tile is processed
     __syncthreads();
 
     // 2. location map with this image's b: l = 1 where the top b bits differ from the
@@ -324,12 +328,25 @@ void launch_topmap(const Batch& B, bool owner, cudaStream_t st) {
 }
 void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_strips == 0) return;
+  // whole tile rows per CTA (the next tile's fetch hides the current one's latency),
+  // split when the batch has fewer rows than ~4 CTAs per SM slot
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const uint32_t want = (uint32_t)sms * 6u * 4u;
+  uint32_t nsplit = want / B.total_strips;
+  nsplit = nsplit < 1 ? 1 : nsplit > 64 ? 64 : nsplit;
+  const uint32_t grid = B.total_strips * nsplit;
   if (any_med) {
-    if (any_lmr) k_enc_strip<true, true><<<B.total_strips, 256, 0, st>>>(B);
-    else k_enc_strip<false, true><<<B.total_strips, 256, 0, st>>>(B);
+    if (any_lmr) k_enc_rows<true, true><<<grid, 256, 0, st>>>(B, nsplit);
+    else k_enc_rows<false, true><<<grid, 256, 0, st>>>(B, nsplit);
   } else {
-    if (any_lmr) k_enc_strip<true, false><<<B.total_strips, 256, 0, st>>>(B);
-    else k_enc_strip<false, false><<<B.total_strips, 256, 0, st>>>(B);
+    if (any_lmr) k_enc_rows<true, false><<<grid, 256, 0, st>>>(B, nsplit);
+    else k_enc_rows<false, false><<<grid, 256, 0, st>>>(B, nsplit);
   }
 }
 

@@ -234,6 +234,13 @@ class Plan:
         """Stages of op that launch work for this plan's jobs."""
         return [s for s in range(len(stages(op))) if _lib.rdhei_plan_stage_active(self._h, int(op), s)]
 
+    def error_word(self) -> torch.Tensor:
+        """The workspace error word (4 device bytes, an rdhei_status code once the
+        plan's work has finished) as a tensor view, for an asynchronous copy to the
+        host; status() reads it synchronously."""
+        off = self._ws_ptr - self.ws.data_ptr()
+        return self.ws[off:off + 4]
+
     def status(self, stream=None) -> int:
         code = ctypes.c_int32(0)
         _check(_lib.rdhei_workspace_status(ctypes.c_void_p(self._ws_ptr), _stream(stream), ctypes.byref(code)),

@@ -23,6 +23,8 @@ the error text is in Request.error).  Every request ends in exactly one of them.
 """
 from __future__ import annotations
 
+import functools
+import gc
 import json
 import math
 import time
@@ -52,16 +54,21 @@ class Request:
     error: str = ""
     result: dict = field(default_factory=dict)
 
-    @property
+    @functools.cached_property
     def pixels(self) -> int:
-        return int(np.prod(tuple(self.image.shape)))
+        H, W = self.image.shape
+        return int(H) * int(W)
 
-    def device_bytes(self) -> int:
-        """Device memory the request holds while in flight (buffers + workspace share)."""
+    @functools.cached_property
+    def _bytes(self) -> int:
         N = self.pixels
         words = ((N + 31) // 32) * 4
         msg = ((self.nbits + 31) // 32) * 4 + 4
         return 4 * N + 2 * words + 2 * msg + N + N // 4 + 4096
+
+    def device_bytes(self) -> int:
+        """Device memory the request holds while in flight (buffers + workspace share)."""
+        return self._bytes
 
 
 class _InFlight:
@@ -217,6 +224,18 @@ class Scheduler:
         if not realtime:
             for r in pending:
                 r.arrival = 0.0
+        # no cyclic garbage collection inside the loop: a full collection over the
+        # requests' objects pauses the loop for milliseconds (a latency tail)
+        gc_was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            self._loop(pending)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+        return self.completed
+
+    def _loop(self, pending: deque):
         while pending or self.queue or self.inflight:
             now = self.now()
             while pending and pending[0].arrival <= now:
@@ -238,7 +257,6 @@ class Scheduler:
                 time.sleep(max(0.0, min(pending[0].arrival - self.now(), 2e-4)))
             elif self.queue and self.inflight:
                 time.sleep(2e-5)                  # the budget is held by running batches
-        return self.completed
 
     # ---------------------------------------------------------------- metrics --
     def metrics(self) -> dict:

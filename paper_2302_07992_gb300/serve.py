@@ -58,7 +58,7 @@ class _Batch:
         self.event = torch.cuda.Event()
         self.keep = []          # device tensors and plans alive until completion
         self.plans = []
-        self.outs, self.hinfo = None, None
+        self.outs, self.hinfo, self.hcodes = None, None, None
 
 
 class CudaExecutor:
@@ -104,15 +104,25 @@ class CudaExecutor:
         infos = rd.read_info(bt.hinfo)
         self.pool.give(bt.hinfo)
         bt.hinfo = None
-        # the workspace error word of each plan: a device-side failure (timeout, index
-        # check) fails the whole batch; ECAPACITY is a per-request outcome
-        for pl in bt.plans:
-            code = pl.status(bt.stream)
+        # the plans' workspace error words came down with the results: a device-side
+        # failure (timeout, index check) fails the whole batch; ECAPACITY is a
+        # per-request outcome
+        codes = [int(c) for c in bt.hcodes.view(torch.int32).tolist()]
+        self.pool.give(bt.hcodes)
+        bt.hcodes = None
+        for code in codes:
             if code not in (0, rd.RDHEI_ECAPACITY):
                 for o in bt.outs:
                     self.discard(o)
                 raise rd.RdheiError(f"device reported {rd.STATUS.get(code, code)}")
         return [{**o, "info": inf} for o, inf in zip(bt.outs, infos)]
+
+    def _error_words(self, *plans) -> torch.Tensor:
+        """Pinned copies of the plans' error words, read once the batch's event fired."""
+        h = self.pool.take((4 * len(plans),))
+        for i, pl in enumerate(plans):
+            h[4 * i:4 * i + 4].copy_(pl.error_word(), non_blocking=True)
+        return h
 
     def discard(self, result: dict):
         for v in list(result.values()):
@@ -157,6 +167,7 @@ class CudaExecutor:
             outs.append(o)
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
+        bt.hcodes = self._error_words(p1, p2)
         bt.keep += [imgs, enc, marked, maps, etas, pays]
         bt.plans = [p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
@@ -190,6 +201,7 @@ class CudaExecutor:
             outs.append({"bits": hb, "recovered": hr})
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
+        bt.hcodes = self._error_words(p1, p2)
         bt.keep += [imgs, rec, maps, etas, bits]
         bt.plans = [p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
