@@ -347,6 +347,13 @@ int rdhei_wait_selftest(const uint32_t *flag, uint64_t limit_ns, int32_t *status
  * (synchronises the stream).  0 = no error, else an rdhei_status code. */
 int rdhei_workspace_status(void *ws, void *stream, int32_t *code);
 
+/* The same word without synchronising: queues a 4-byte copy of the uploaded plan's
+ * workspace error word to dst (pinned host or device memory, 4-byte aligned) on
+ * `stream`, behind the plan's work queued there; dst holds the code once the stream
+ * reaches the copy.  Returns RDHEI_EINVAL for a null or misaligned dst or a plan not
+ * uploaded, RDHEI_ECUDA for a failed copy. */
+int rdhei_plan_copy_status(const rdhei_plan *plan, int32_t *dst, void *stream);
+
 /* sizeof(rdhei_job) and sizeof(rdhei_info), for bindings that build them by hand. */
 size_t rdhei_job_size(void);
 size_t rdhei_info_size(void);

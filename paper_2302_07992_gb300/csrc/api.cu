@@ -513,6 +513,13 @@ int rdhei_workspace_status(void* ws, void* stream, int32_t* code) {
   return RDHEI_OK;
 }
 
+int rdhei_plan_copy_status(const rdhei_plan* p, int32_t* dst, void* stream) {
+  if (!p || !p->ws || !dst || (reinterpret_cast<uintptr_t>(dst) & 3)) return RDHEI_EINVAL;
+  const uint8_t* w = reinterpret_cast<const uint8_t*>(p->ws) + p->off_err;
+  return cudaMemcpyAsync(dst, w, 4, cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? RDHEI_OK : RDHEI_ECUDA;
+}
+
 size_t rdhei_job_size(void) { return sizeof(rdhei_job); }
 size_t rdhei_info_size(void) { return sizeof(rdhei_info); }
 

@@ -87,6 +87,8 @@ _lib.rdhei_info_size.restype = ctypes.c_size_t
 _lib.rdhei_version.restype = ctypes.c_char_p
 _lib.rdhei_build_flags.argtypes = []
 _lib.rdhei_build_flags.restype = ctypes.c_int
+_lib.rdhei_plan_copy_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rdhei_plan_copy_status.restype = ctypes.c_int
 _lib.rdhei_wait_selftest.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
 _lib.rdhei_wait_selftest.restype = ctypes.c_int
 
@@ -234,12 +236,13 @@ class Plan:
         """Stages of op that launch work for this plan's jobs."""
         return [s for s in range(len(stages(op))) if _lib.rdhei_plan_stage_active(self._h, int(op), s)]
 
-    def error_word(self) -> torch.Tensor:
-        """The workspace error word (4 device bytes, an rdhei_status code once the
-        plan's work has finished) as a tensor view, for an asynchronous copy to the
-        host; status() reads it synchronously."""
-        off = self._ws_ptr - self.ws.data_ptr()
-        return self.ws[off:off + 4]
+    def copy_status(self, dst: torch.Tensor, stream=None):
+        """Queue a copy of the workspace error word into dst (an int32 element of
+        pinned host or device memory) behind this plan's work on `stream`; status()
+        reads it synchronously instead."""
+        assert dst.dtype == torch.int32 and dst.numel() >= 1 and (dst.is_cuda or dst.is_pinned())
+        _check(_lib.rdhei_plan_copy_status(self._h, ctypes.c_void_p(dst.data_ptr()), _stream(stream)),
+               "rdhei_plan_copy_status")
 
     def status(self, stream=None) -> int:
         code = ctypes.c_int32(0)

@@ -18,9 +18,9 @@ ranges.
 """
 from __future__ import annotations
 
+import math
 from collections import deque
 
-import numpy as np
 import torch
 
 from . import rdhei as rd
@@ -40,7 +40,7 @@ class PinnedPool:
         return max(4096, 1 << (max(int(nbytes), 1) - 1).bit_length())
 
     def take(self, shape) -> torch.Tensor:
-        nbytes = int(np.prod(shape)) if len(shape) else 1
+        nbytes = math.prod(int(x) for x in shape) if len(shape) else 1
         c = self._cls(nbytes)
         lst = self.free.get(c)
         buf = lst.pop() if lst else torch.empty(c, dtype=torch.uint8, pin_memory=True)
@@ -79,12 +79,10 @@ class CudaExecutor:
         torch.cuda.nvtx.range_push(f"serve.{reqs[0].kind}[{len(reqs)}]")
         try:
             with torch.cuda.stream(st):
-                info = rd.new_info(len(reqs), dev)
-                bt.keep.append(info)
                 if reqs[0].kind == "encode":
-                    self._launch_encode(bt, reqs, info, st, dev)
+                    self._launch_encode(bt, reqs, st, dev)
                 else:
-                    self._launch_decode(bt, reqs, info, st, dev)
+                    self._launch_decode(bt, reqs, st, dev)
                 bt.event.record(st)
         except Exception:
             st.synchronize()                    # nothing of this batch may still use its buffers
@@ -107,7 +105,7 @@ class CudaExecutor:
         # the plans' workspace error words came down with the results: a device-side
         # failure (timeout, index check) fails the whole batch; ECAPACITY is a
         # per-request outcome
-        codes = [int(c) for c in bt.hcodes.view(torch.int32).tolist()]
+        codes = bt.hcodes.tolist()
         self.pool.give(bt.hcodes)
         bt.hcodes = None
         for code in codes:
@@ -119,14 +117,15 @@ class CudaExecutor:
 
     def _error_words(self, *plans) -> torch.Tensor:
         """Pinned copies of the plans' error words, read once the batch's event fired."""
-        h = self.pool.take((4 * len(plans),))
+        h = self.pool.take((4 * len(plans),)).view(torch.int32)
+        st = torch.cuda.current_stream()
         for i, pl in enumerate(plans):
-            h[4 * i:4 * i + 4].copy_(pl.error_word(), non_blocking=True)
+            pl.copy_status(h[i:i + 1], st)
         return h
 
     def discard(self, result: dict):
-        for v in list(result.values()):
-            if isinstance(v, torch.Tensor) and v.is_pinned():
+        for v in result.values():
+            if isinstance(v, torch.Tensor):          # result tensors all come from the pool
                 self.pool.give(v)
 
     def release(self, bt: _Batch):
@@ -134,15 +133,34 @@ class CudaExecutor:
         bt.plans.clear()
         self.free_streams.append(bt.stream)
 
-    def _launch_encode(self, bt, reqs, info, st, dev):
+    def _arena(self, sizes, zero: bool, dev):
+        """One device allocation cut into 256-byte-aligned pieces of the given sizes
+        (None for a size of None); zero-filled when the kernels OR into it."""
+        offs, tot = [], 0
+        for n in sizes:
+            offs.append(None if n is None else tot)
+            if n is not None:
+                tot += (int(n) + 255) & ~255
+        buf = (torch.zeros if zero else torch.empty)(max(tot, 256), dtype=torch.uint8, device=dev)
+        return buf, [None if o is None else buf[o:o + int(n)] for o, n in zip(offs, sizes)]
+
+    @staticmethod
+    def _words(nbits: int) -> int:
+        return max(4, ((int(nbits) + 31) // 32) * 4)
+
+    def _launch_encode(self, bt, reqs, st, dev):
         # buffers and plans first (a plan upload waits for its stream), then copies and work
-        imgs = [torch.empty(r.image.shape, dtype=torch.uint8, device=dev) for r in reqs]
-        enc = [torch.empty_like(x) for x in imgs]
-        marked = [torch.empty_like(x) for x in imgs]
+        n = len(reqs)
+        px = [r.pixels for r in reqs]
         lmr = [(r.params.variant & 1) == rd.LMR for r in reqs]
-        maps = [rd.bitbuf(x.numel(), dev) if l else None for x, l in zip(imgs, lmr)]
-        etas = [rd.bitbuf(x.numel(), dev) if l else None for x, l in zip(imgs, lmr)]
-        pays = [rd.bitbuf(r.nbits, dev) for r in reqs]
+        img_arena, views = self._arena(px * 3, False, dev)
+        imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
+        enc = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
+        marked = [v.view(*r.image.shape) for v, r in zip(views[2 * n:], reqs)]
+        bit_arena, bviews = self._arena([self._words(p) if l else None for p, l in zip(px, lmr)] * 2 +
+                                        [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
+        maps, etas, pays = bviews[:n], bviews[n:2 * n], bviews[2 * n:3 * n]
+        info = bviews[-1].view(n, rd.INFO_BYTES)
         j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=enc[i], map_bits=maps[i], eta_bits=etas[i],
                           info=info[i]) for i, r in enumerate(reqs)]
         j2 = [rd.make_job(r.params, *r.image.shape, src=enc[i], dst=marked[i], map_bits=maps[i], payload=pays[i],
@@ -168,18 +186,21 @@ class CudaExecutor:
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
         bt.hcodes = self._error_words(p1, p2)
-        bt.keep += [imgs, enc, marked, maps, etas, pays]
+        bt.keep += [img_arena, bit_arena]
         bt.plans = [p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
 
-    def _launch_decode(self, bt, reqs, info, st, dev):
-        imgs = [torch.empty(r.image.shape, dtype=torch.uint8, device=dev) for r in reqs]
-        rec = [torch.empty_like(x) for x in imgs]
-        maps = [torch.empty(r.lmr_map.shape, dtype=torch.uint8, device=dev) if r.lmr_map is not None else None
-                for r in reqs]
-        etas = [torch.empty(r.lmr_eta.shape, dtype=torch.uint8, device=dev) if r.lmr_eta is not None else None
-                for r in reqs]
-        bits = [rd.bitbuf(r.nbits, dev) for r in reqs]
+    def _launch_decode(self, bt, reqs, st, dev):
+        n = len(reqs)
+        px = [r.pixels for r in reqs]
+        img_arena, views = self._arena(px * 2 + [r.lmr_map.numel() if r.lmr_map is not None else None for r in reqs]
+                                       + [r.lmr_eta.numel() if r.lmr_eta is not None else None for r in reqs],
+                                       False, dev)
+        imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
+        rec = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
+        maps, etas = views[2 * n:3 * n], views[3 * n:]
+        bit_arena, bviews = self._arena([self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
+        bits, info = bviews[:n], bviews[-1].view(n, rd.INFO_BYTES)
         j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], map_bits=maps[i], bits_out=bits[i], max_bits=r.nbits,
                           info=info[i], b=r.b) for i, r in enumerate(reqs)]
         j2 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=rec[i], map_bits=maps[i], eta_bits=etas[i],
@@ -188,8 +209,8 @@ class CudaExecutor:
         for i, r in enumerate(reqs):
             imgs[i].copy_(r.image, non_blocking=True)
             if maps[i] is not None:
-                maps[i].copy_(r.lmr_map, non_blocking=True)
-                etas[i].copy_(r.lmr_eta, non_blocking=True)
+                maps[i].copy_(r.lmr_map.reshape(-1), non_blocking=True)
+                etas[i].copy_(r.lmr_eta.reshape(-1), non_blocking=True)
         p1.run(rd.OP_EXTRACT, st)
         p2.run(rd.OP_DECRYPT_RECOVER, st)
         outs = []
@@ -202,7 +223,7 @@ class CudaExecutor:
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
         bt.hcodes = self._error_words(p1, p2)
-        bt.keep += [imgs, rec, maps, etas, bits]
+        bt.keep += [img_arena, bit_arena]
         bt.plans = [p1, p2]
         bt.outs, bt.hinfo = outs, hinfo
 
