@@ -828,7 +828,9 @@ def roofline(res, peaks, args):
     return roof, out_all
 
 
-HOT_PATH_SOURCES = ("api.cu", "common.cuh", "decode.cu", "encode.cu", "hide.cu", "pass1.cu", "permute.cuh")
+# the timed kernels and their launchers (host-only ABI code in api.cu does not change
+# what the kernels move)
+HOT_PATH_SOURCES = ("common.cuh", "decode.cu", "encode.cu", "hide.cu", "pass1.cu", "permute.cuh")
 
 
 def kernel_source_hash() -> str:
