@@ -330,13 +330,9 @@ void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t s
   if (B.total_strips == 0) return;
   // whole tile rows per CTA (the next tile's fetch hides the current one's latency),
   // split when the batch has fewer rows than ~4 CTAs per SM slot
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
   const uint32_t want = (uint32_t)sms * 6u * 4u;
   uint32_t nsplit = want / B.total_strips;
   nsplit = nsplit < 1 ? 1 : nsplit > 64 ? 64 : nsplit;
