@@ -275,11 +275,33 @@ def run_gpu(args, rank, world, local_rank):
     verify = verify_batch(args, rd, imgs, enc, marked, rec, maps, etas, payload, bits_out, info, caps, variants,
                           params, first, imgs_np, side_np)
 
-    # timed region: K steps, an event after every kernel
+    # per-kernel breakdown: a short run with an event after every kernel.  An event
+    # between two kernels ends their programmatic overlap, so this run only splits the
+    # step into kernels and picks the dominant one; the timed region below has events
+    # around that kernel alone.
     import torch.distributed as dist
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in stage_list] for _ in range(K)]
-    start = torch.cuda.Event(enable_timing=True)
+    K2 = min(K, 20)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in stage_list] for _ in range(K2)]
+    b0 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    b0.record(stream)
+    for k in range(K2):
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    per_stage = {}
+    for k in range(K2):
+        for i, (_, op, s, name) in enumerate(stage_list):
+            t0 = b0 if (k == 0 and i == 0) else (evs[k][i - 1] if i > 0 else evs[k - 1][-1])
+            per_stage.setdefault(name, []).append(t0.elapsed_time(evs[k][i]))
+    tot = {nm: sum(v) for nm, v in per_stage.items()}
+    dom = max(tot, key=tot.get)
+    i_dom = [x[3] for x in stage_list].index(dom)
+
+    # timed region: K steps; events only before and after the dominant kernel
+    dom_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    dom_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -287,17 +309,18 @@ def run_gpu(args, rank, world, local_rank):
         time.sleep(0.3)  # let the sampler start
         start.record(stream)
         for k in range(K):
-            step(evs[k])
+            for i, (pl, op, s_, _) in enumerate(stage_list):
+                if i == i_dom:
+                    dom_a[k].record(stream)
+                pl.run_stage(op, s_, stream)
+                if i == i_dom:
+                    dom_b[k].record(stream)
+        end.record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
-    total_ms = start.elapsed_time(evs[-1][-1])
-    per_stage = {}
-    prev = None
-    for k in range(K):
-        for i, (_, op, s, name) in enumerate(stage_list):
-            t0 = start if (k == 0 and i == 0) else (evs[k][i - 1] if i > 0 else evs[k - 1][-1])
-            per_stage.setdefault(name, []).append(t0.elapsed_time(evs[k][i]))
+    total_ms = start.elapsed_time(end)
+    dom_ms = sum(a.elapsed_time(b) for a, b in zip(dom_a, dom_b)) / K
     total_ms = max_over_ranks(total_ms, world, dev)
     px_step = n * N
     value = job_throughput(px_step, world, K, total_ms)
@@ -307,7 +330,8 @@ def run_gpu(args, rank, world, local_rank):
     e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec, wave_cols)
 
     clocks = clk.summary()
-    return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "px_step": px_step,
+    return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "K_breakdown": K2,
+            "dominant": dom, "dominant_ms": dom_ms, "px_step": px_step,
             "verify": verify, "e2e": e2e, "clocks": clocks, "stage_list": [x[3] for x in stage_list],
             "caps": caps, "variants": variants, "tuning": tuning}
 
@@ -776,10 +800,10 @@ ALU_OPS_PER_KS_BYTE = 10.0     # ChaCha20: (4 XOR + 4 rotate) per quarter-round,
 
 def roofline(res, peaks, args):
     """Roofline of the dominant kernel (largest share of the timed region)."""
-    K = res["K"]
+    K = res["K_breakdown"]
     tot = {k: sum(v) for k, v in res["per_stage"].items()}
-    dom = max(tot, key=tot.get)
-    avg_ms = tot[dom] / K
+    dom = res["dominant"]
+    avg_ms = res["dominant_ms"]          # from the timed region
     n, N = args.images, args.size * args.size
     der = res["verify"]["mean_der_bpp"]
     px = n * N
@@ -808,7 +832,7 @@ def roofline(res, peaks, args):
     hbm_peak = peaks.get("hbm_gbs", 6777.0)
     out_all = {}
     for name, t in tot.items():
-        a_ms = t / K
+        a_ms = avg_ms if name == dom else t / K       # the dominant kernel: timed-region events
         hb = hbm_bytes.get(name, 0.0) / (a_ms / 1e3) / 1e9
         alu = ks_bytes.get(name, 0.0) * ALU_OPS_PER_KS_BYTE / (a_ms / 1e3)
         out_all[name] = {"ms": a_ms, "share": t / sum(tot.values()), "hbm_gbs": hb, "hbm_frac": hb / hbm_peak,
@@ -950,10 +974,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator standing in for BOWS-2)",
             "config": config, "e2e": res["e2e"], "roofline": roof, "cpu_baseline": cpu_base,
-            "clocks": res["clocks"], "gpu_launches": len(res["stage_list"]) * K,
+            "clocks": res["clocks"],
+            "gpu_launches": sum(2 if nm in ("embed_count", "extract_count") else 1 for nm in res["stage_list"]) * K,
             "hbm_roofline_mpx": peaks.get("hbm_gbs", 6777.0) * 1e3 / (4.0 + 2 * res["verify"]["mean_der_bpp"] / 8),
             "verify": res["verify"],
-            "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()}}
+            "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()},
+            "kernels_note": f"per-kernel times from a separate {res['K_breakdown']}-step run with an event after "
+                            "every kernel (an event ends two kernels' programmatic overlap); the timed region has "
+                            "events only around the dominant kernel"}
     if res.get("tuning"):
         line["tuning"] = res["tuning"]
     if rank == 0:

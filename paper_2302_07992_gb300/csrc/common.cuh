@@ -16,6 +16,32 @@
 
 namespace rdhei {
 
+// Programmatic dependent launch (sm_90+).  The kernels of one operation are launched
+// with programmatic stream serialisation: a kernel's CTAs may be scheduled while the
+// previous kernel's last CTAs still run.  Every such kernel calls pdl_wait() before it
+// reads or writes anything the previous kernel touches (the wait returns once that
+// grid has completed and its writes are visible; at once when there is no programmatic
+// predecessor), and pdl_trigger() only after its own wait, so that a kernel that
+// starts early finds every kernel before its predecessor complete.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Host-side NVTX range for the lifetime of a scope (one ABI call or one stage); with
 // no profiler attached a push / pop is a check of an unset function pointer.
 struct NvtxRange {

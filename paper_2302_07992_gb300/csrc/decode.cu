@@ -15,6 +15,8 @@ namespace rdhei {
 
 template <bool ANY_LMR, bool ANY_MED>
 __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t ain[TILE * TPITCH];
   __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
@@ -201,11 +203,11 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
 void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_strips == 0) return;
   if (any_med) {
-    if (any_lmr) k_dec_strip<true, true><<<B.total_strips, 256, 0, st>>>(B);
-    else k_dec_strip<false, true><<<B.total_strips, 256, 0, st>>>(B);
+    if (any_lmr) launch_pdl(k_dec_strip<true, true>, dim3(B.total_strips), dim3(256), 0, st, B);
+    else launch_pdl(k_dec_strip<false, true>, dim3(B.total_strips), dim3(256), 0, st, B);
   } else {
-    if (any_lmr) k_dec_strip<true, false><<<B.total_strips, 256, 0, st>>>(B);
-    else k_dec_strip<false, false><<<B.total_strips, 256, 0, st>>>(B);
+    if (any_lmr) launch_pdl(k_dec_strip<true, false>, dim3(B.total_strips), dim3(256), 0, st, B);
+    else launch_pdl(k_dec_strip<false, false>, dim3(B.total_strips), dim3(256), 0, st, B);
   }
 }
 

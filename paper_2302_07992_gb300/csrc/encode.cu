@@ -20,6 +20,8 @@ __device__ __forceinline__ int top_off(int H, int W, int L) {
 //   both:     sums of the tile totals up the levels above 6 (Eq. roration) and, per
 //             tile, where the composed rotation sends it and the angle sum above 6.
 __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   __shared__ uint8_t top[TOP_SMEM];
   const int img = blockIdx.x;
   const ImgDesc& d = B.desc[img];
@@ -107,6 +109,8 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
 // ---------------------------------------------------------------------------------
 template <bool ANY_LMR, bool ANY_MED>
 __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint32_t nsplit) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
   __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
   __shared__ __align__(16) uint8_t lin[ANY_LMR ? TILE * TPITCH : 16];
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
 
 void launch_topmap(const Batch& B, bool owner, cudaStream_t st) {
   if (B.n_images == 0) return;
-  k_topmap<<<B.n_images, 256, 0, st>>>(B, owner ? 1 : 0);
+  launch_pdl(k_topmap, dim3(B.n_images), dim3(256), 0, st, B, owner ? 1 : 0);
 }
 void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_strips == 0) return;
@@ -338,11 +342,11 @@ void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t s
   nsplit = nsplit < 1 ? 1 : nsplit > 64 ? 64 : nsplit;
   const uint32_t grid = B.total_strips * nsplit;
   if (any_med) {
-    if (any_lmr) k_enc_rows<true, true><<<grid, 256, 0, st>>>(B, nsplit);
-    else k_enc_rows<false, true><<<grid, 256, 0, st>>>(B, nsplit);
+    if (any_lmr) launch_pdl(k_enc_rows<true, true>, dim3(grid), dim3(256), 0, st, B, nsplit);
+    else launch_pdl(k_enc_rows<false, true>, dim3(grid), dim3(256), 0, st, B, nsplit);
   } else {
-    if (any_lmr) k_enc_rows<true, false><<<grid, 256, 0, st>>>(B, nsplit);
-    else k_enc_rows<false, false><<<grid, 256, 0, st>>>(B, nsplit);
+    if (any_lmr) launch_pdl(k_enc_rows<true, false>, dim3(grid), dim3(256), 0, st, B, nsplit);
+    else launch_pdl(k_enc_rows<false, false>, dim3(grid), dim3(256), 0, st, B, nsplit);
   }
 }
 

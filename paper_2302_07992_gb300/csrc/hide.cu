@@ -161,6 +161,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 // whose LSB (the location-map bit) is 0, LMR the 0 bits of the packed map.
 constexpr int COUNT_WARPS = 8;
 __global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const uint32_t g = blockIdx.x * COUNT_WARPS + (threadIdx.x >> 5);
   if (g >= B.total_chunks) return;
@@ -218,6 +220,8 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) {
 // extractor, clearing of the output words shared by two chunks.
 template <bool EXTRACT>
 __global__ void __launch_bounds__(HIDE_THREADS) k_offsets(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
   const int t = threadIdx.x;
   const int img = blockIdx.x;
@@ -265,6 +269,8 @@ __global__ void __launch_bounds__(HIDE_THREADS) k_offsets(Batch B) {
 // were cleared by k_offsets).
 template <bool EXTRACT>
 __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   constexpr int EW = (SBUF_WORDS + HIDE_THREADS - 1) / HIDE_THREADS;   // message words per thread
   __shared__ uint32_t sbuf[SBUF_WORDS];   // hider: e words (MSB-first); receiver: raw slot stream
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
@@ -488,6 +494,10 @@ __global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
   if (w0 >= nwords) return;
   uint32_t o[16];
   chacha20_block(d.k2, blk, d.n2, o, d.one);
+  // the keystream needs nothing from the previous kernel (the receiver's bit count
+  // comes from the kernel before it); the message does
+  pdl_wait();
+  pdl_trigger();
   const uint32_t* in = reinterpret_cast<const uint32_t*>(DECRYPT ? d.bits_out : d.payload);
   uint32_t* out = reinterpret_cast<uint32_t*>(DECRYPT ? d.bits_out : d.ebuf);
   const int nw = (int)umin64(16, nwords - w0);
@@ -515,6 +525,8 @@ __global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
 
 // LMR side information into bit 7 (Sec. III-B-1): pixel q < side_nbits.
 __global__ void k_lmr_side(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   const uint32_t g = blockIdx.x;
   const int img = owner_of(B.chunk_prefix, B.n_images, g);
   const ImgDesc& d = B.desc[img];
@@ -539,24 +551,24 @@ static int persistent_grid(K kernel, uint32_t work) {
 // count + per-image offsets
 void launch_count(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
-  k_count<<<(B.total_chunks + COUNT_WARPS - 1) / COUNT_WARPS, 32 * COUNT_WARPS, 0, st>>>(B);
-  if (extract) k_offsets<true><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
-  else k_offsets<false><<<B.n_images, HIDE_THREADS, 0, st>>>(B);
+  launch_pdl(k_count, dim3((B.total_chunks + COUNT_WARPS - 1) / COUNT_WARPS), dim3(32 * COUNT_WARPS), 0, st, B);
+  if (extract) launch_pdl(k_offsets<true>, dim3(B.n_images), dim3(HIDE_THREADS), 0, st, B);
+  else launch_pdl(k_offsets<false>, dim3(B.n_images), dim3(HIDE_THREADS), 0, st, B);
 }
 void launch_scan(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
-  if (extract) k_scan<true><<<persistent_grid(k_scan<true>, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
-  else k_scan<false><<<persistent_grid(k_scan<false>, B.total_chunks), HIDE_THREADS, 0, st>>>(B);
+  if (extract) launch_pdl(k_scan<true>, dim3(persistent_grid(k_scan<true>, B.total_chunks)), dim3(HIDE_THREADS), 0, st, B);
+  else launch_pdl(k_scan<false>, dim3(persistent_grid(k_scan<false>, B.total_chunks)), dim3(HIDE_THREADS), 0, st, B);
 }
 void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st) {
   if (B.total_z2_blocks == 0) return;
   const uint32_t grid = (B.total_z2_blocks + 127) / 128;
-  if (decrypt) k_z2_xor<true><<<grid, 128, 0, st>>>(B);
-  else k_z2_xor<false><<<grid, 128, 0, st>>>(B);
+  if (decrypt) launch_pdl(k_z2_xor<true>, dim3(grid), dim3(128), 0, st, B);
+  else launch_pdl(k_z2_xor<false>, dim3(grid), dim3(128), 0, st, B);
 }
 void launch_lmr_side(const Batch& B, cudaStream_t st) {
   if (B.total_chunks == 0) return;
-  k_lmr_side<<<B.total_chunks, HIDE_THREADS, 0, st>>>(B);
+  launch_pdl(k_lmr_side, dim3(B.total_chunks), dim3(HIDE_THREADS), 0, st, B);
 }
 
 }  // namespace rdhei

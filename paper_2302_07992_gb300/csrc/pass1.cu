@@ -43,6 +43,8 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
 
 template <int MODE, bool GENERAL, bool ANY_MED>
 __global__ void __launch_bounds__(64) k_pass1(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
   // keystream staging for rows that straddle two ChaCha blocks (W not a multiple of 64)
   __shared__ uint32_t ks_stage[GENERAL ? 64 : 1][33];
   __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
@@ -360,15 +362,15 @@ void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStre
   if (B.total_tiles == 0) return;
   if (mode == MODE_ENC) {
     if (any_med) {
-      if (general) k_pass1<MODE_ENC, true, true><<<B.total_tiles, 64, 0, st>>>(B);
-      else k_pass1<MODE_ENC, false, true><<<B.total_tiles, 64, 0, st>>>(B);
+      if (general) launch_pdl(k_pass1<MODE_ENC, true, true>, dim3(B.total_tiles), dim3(64), 0, st, B);
+      else launch_pdl(k_pass1<MODE_ENC, false, true>, dim3(B.total_tiles), dim3(64), 0, st, B);
     } else {
-      if (general) k_pass1<MODE_ENC, true, false><<<B.total_tiles, 64, 0, st>>>(B);
-      else k_pass1<MODE_ENC, false, false><<<B.total_tiles, 64, 0, st>>>(B);
+      if (general) launch_pdl(k_pass1<MODE_ENC, true, false>, dim3(B.total_tiles), dim3(64), 0, st, B);
+      else launch_pdl(k_pass1<MODE_ENC, false, false>, dim3(B.total_tiles), dim3(64), 0, st, B);
     }
   } else {
-    if (general) k_pass1<MODE_DEC, true, false><<<B.total_tiles, 64, 0, st>>>(B);
-    else k_pass1<MODE_DEC, false, false><<<B.total_tiles, 64, 0, st>>>(B);
+    if (general) launch_pdl(k_pass1<MODE_DEC, true, false>, dim3(B.total_tiles), dim3(64), 0, st, B);
+    else launch_pdl(k_pass1<MODE_DEC, false, false>, dim3(B.total_tiles), dim3(64), 0, st, B);
   }
 }
 
