@@ -12,6 +12,7 @@ namespace rdhei {
 void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStream_t st);
 void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
 void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 void launch_count(const Batch& B, bool extract, cudaStream_t st);
 void launch_scan(const Batch& B, bool extract, cudaStream_t st);
@@ -382,7 +383,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
     int rc = check_op(p, op);
     if (rc) return rc;
     uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
-    if (cudaMemsetAsync(base + p->off_zero, 0, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
+    if (launch_zero(base + p->off_zero, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
     if (op == RDHEI_OP_LABEL_ENCRYPT) {
       // packed-map outputs of images whose rows do not start on a 16-bit boundary are
       // OR-ed word by word and must start from zero

@@ -357,6 +357,24 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
   }
 }
 
+// The workspace's zero region (error word, tickets, counters, flags), cleared at the
+// start of every operation by a kernel rather than a memset, so that the chain of
+// programmatically dependent launches runs on from the previous operation.
+__global__ void __launch_bounds__(256) k_zero(uint4* p, uint32_t n16) {
+  pdl_wait();      // the previous kernel may still use this workspace
+  pdl_trigger();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x)
+    p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(p) & 15) || (bytes & 15)) return cudaMemsetAsync(p, 0, bytes, st);
+  const uint32_t n16 = (uint32_t)(bytes / 16);
+  uint32_t grid = (n16 + 255) / 256;
+  if (grid > 1216) grid = 1216;
+  return launch_pdl(k_zero, dim3(grid), dim3(256), 0, st, reinterpret_cast<uint4*>(p), n16);
+}
+
 // general = some image has W % 64 != 0 or a ragged tile row (rows that straddle blocks)
 void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStream_t st) {
   if (B.total_tiles == 0) return;
