@@ -332,6 +332,10 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
     return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "K_breakdown": K2,
             "dominant": dom, "dominant_ms": dom_ms, "px_step": px_step,
+            # kernels per step: one per stage, plus the zero-region clear of every
+            # operation's first stage and the offsets kernel of the two count stages
+            "kernels_per_step": sum(1 + (s_ == 0) + (nm in ("embed_count", "extract_count"))
+                                    for _, _, s_, nm in stage_list),
             "verify": verify, "e2e": e2e, "clocks": clocks, "stage_list": [x[3] for x in stage_list],
             "caps": caps, "variants": variants, "tuning": tuning}
 
@@ -975,7 +979,7 @@ def main():
             "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded generator standing in for BOWS-2)",
             "config": config, "e2e": res["e2e"], "roofline": roof, "cpu_baseline": cpu_base,
             "clocks": res["clocks"],
-            "gpu_launches": sum(2 if nm in ("embed_count", "extract_count") else 1 for nm in res["stage_list"]) * K,
+            "gpu_launches": res["kernels_per_step"] * K,
             "hbm_roofline_mpx": peaks.get("hbm_gbs", 6777.0) * 1e3 / (4.0 + 2 * res["verify"]["mean_der_bpp"] / 8),
             "verify": res["verify"],
             "kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items()},
