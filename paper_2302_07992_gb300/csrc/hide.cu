@@ -488,16 +488,17 @@ __global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
   const ImgDesc& d = B.desc[img];
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
   const uint32_t blk = j - __ldg(B.z2_prefix + img);
+  // the keystream block needs nothing that an earlier kernel writes: it is computed
+  // while the previous kernel finishes; the bit count and the message are read after
+  // the wait
+  uint32_t o[16];
+  chacha20_block(d.k2, blk, d.n2, o, d.one);
+  pdl_wait();
+  pdl_trigger();
   const uint64_t nbits = DECRYPT ? info->extracted : d.nbits;
   const uint64_t nwords = (nbits + 31) >> 5;
   const uint64_t w0 = (uint64_t)blk * 16;
   if (w0 >= nwords) return;
-  uint32_t o[16];
-  chacha20_block(d.k2, blk, d.n2, o, d.one);
-  // the keystream needs nothing from the previous kernel (the receiver's bit count
-  // comes from the kernel before it); the message does
-  pdl_wait();
-  pdl_trigger();
   const uint32_t* in = reinterpret_cast<const uint32_t*>(DECRYPT ? d.bits_out : d.payload);
   uint32_t* out = reinterpret_cast<uint32_t*>(DECRYPT ? d.bits_out : d.ebuf);
   const int nw = (int)umin64(16, nwords - w0);
