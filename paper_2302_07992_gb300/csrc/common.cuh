@@ -132,13 +132,27 @@ struct Batch {
 constexpr int WAVE_ROWS = 32, WAVE_COLS_DEFAULT = 128;
 
 // Median edge detector on four bytes at once (related-work predictor, LOCO-I):
-// min(A, B) where C >= max(A, B), max(A, B) where C <= min(A, B), else A + B - C
-// (which then lies between min and max, so the bytewise wrap-around never triggers).
+// min(A, B) where C >= max(A, B), max(A, B) where C <= min(A, B), else A + B - C.
+// The same value is min + max - clamp(C, min, max), which never leaves [min, max];
+// it is computed on the even and the odd bytes as 16-bit lanes with the hardware
+// two-lane min / max.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t med2(uint32_t a, uint32_t b, uint32_t c) {   // two 16-bit lanes
+  const uint32_t mn = min_u16x2(a, b), mx = max_u16x2(a, b);
+  return mn + mx - min_u16x2(max_u16x2(c, mn), mx);                              // no lane carries
+}
 __device__ __forceinline__ uint32_t med4(uint32_t A, uint32_t Bv, uint32_t C) {
-  const uint32_t mx = __vmaxu4(A, Bv), mn = __vminu4(A, Bv);
-  const uint32_t ge = __vcmpgeu4(C, mx), le = __vcmpleu4(C, mn);
-  const uint32_t lin = __vsub4(__vadd4(A, Bv), C);
-  return (ge & mn) | (~ge & le & mx) | (~ge & ~le & lin);
+  const uint32_t M = 0x00FF00FFu;
+  return med2(A & M, Bv & M, C & M) | (med2((A >> 8) & M, (Bv >> 8) & M, (C >> 8) & M) << 8);
 }
 
 // Error codes shared with rdhei.h.

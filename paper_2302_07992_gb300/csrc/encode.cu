@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
         for (int i = 0; i < 4; i++) {
           const uint32_t A = __funnelshift_l(i == 0 ? (left << 24) : w[i - 1], w[i], 8);
           const uint32_t C = __funnelshift_l(i == 0 ? (ul << 24) : up[i - 1], up[i], 8);
-          uint32_t pred = seven ? med4((A >> 1) & 0x7F7F7F7Fu, (up[i] >> 1) & 0x7F7F7F7Fu, (C >> 1) & 0x7F7F7F7Fu) << 1
-                                : med4(A, up[i], C);
+          const uint32_t sh = seven ? 1u : 0u, keep = seven ? 0x7F7F7F7Fu : 0xFFFFFFFFu;   // EMR: top seven bits
+          uint32_t pred = med4((A >> sh) & keep, (up[i] >> sh) & keep, (C >> sh) & keep) << sh;
           if (y == 0) pred = seven ? A & 0xFEFEFEFEu : A;                            // row 0: from the left
           if (i == 0 && x == 0) pred = (pred & 0xFFFFFF00u) | (up[0] & (seven ? 0xFEu : 0xFFu));   // column 0
           uint32_t dd = w[i] ^ pred;
