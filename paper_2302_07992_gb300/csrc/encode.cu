@@ -216,8 +216,9 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
         for (int i = 0; i < 4; i++) {
           const uint32_t A = __funnelshift_l(i == 0 ? (left << 24) : w[i - 1], w[i], 8);
           const uint32_t C = __funnelshift_l(i == 0 ? (ul << 24) : up[i - 1], up[i], 8);
-          const uint32_t sh = seven ? 1u : 0u, keep = seven ? 0x7F7F7F7Fu : 0xFFFFFFFFu;   // EMR: top seven bits
-          uint32_t pred = med4((A >> sh) & keep, (up[i] >> sh) & keep, (C >> sh) & keep) << sh;
+          // EMR: the median of the values with the LSB cleared (twice that of the top seven bits)
+          const uint32_t keep = seven ? 0xFEFEFEFEu : 0xFFFFFFFFu;
+          uint32_t pred = med4(A & keep, up[i] & keep, C & keep);
           if (y == 0) pred = seven ? A & 0xFEFEFEFEu : A;                            // row 0: from the left
           if (i == 0 && x == 0) pred = (pred & 0xFFFFFF00u) | (up[0] & (seven ? 0xFEu : 0xFFu));   // column 0
           uint32_t dd = w[i] ^ pred;

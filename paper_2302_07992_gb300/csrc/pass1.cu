@@ -193,8 +193,9 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
       uint32_t pred = __funnelshift_l(prev, px[i], 8);          // left neighbours
       if (med) {
         const uint32_t Bw = up[i], C = __funnelshift_l(i == 0 ? (ul << 24) : up[i - 1], up[i], 8);
-        const uint32_t sh = seven ? 1u : 0u, keep = seven ? 0x7F7F7F7Fu : 0xFFFFFFFFu;   // EMR: top seven bits
-        uint32_t m = med4((pred >> sh) & keep, (Bw >> sh) & keep, (C >> sh) & keep) << sh;
+        // EMR: the median of the values with the LSB cleared (twice that of the top seven bits)
+        const uint32_t keep = seven ? 0xFEFEFEFEu : 0xFFFFFFFFu;
+        uint32_t m = med4(pred & keep, Bw & keep, C & keep);
         if (y == 0) m = seven ? pred & 0xFEFEFEFEu : pred;      // row 0: from the left
         if (i == 0 && x0 == 0) m = (m & 0xFFFFFF00u) | (Bw & (seven ? 0xFEu : 0xFFu));   // column 0: from above
         pred = m;

@@ -106,20 +106,36 @@ __global__ void __launch_bounds__(32 * WAVE_WARPS) k_med_wave(Batch B) {
     }
     uint32_t o1 = 0;                                           // my last result (left of the next pixel)
     if (tx > 0 && lane < rows) o1 = __ldcg(img + (size_t)(y0 + lane) * W + x0 - 1);
-    uint32_t o0 = o1;                                          // my result one step earlier
+    uint32_t cprev = __shfl_up_sync(0xffffffffu, o1, 1);       // upper-left of my first pixel
     __syncwarp();
 
+    // one pixel per lane and step, branch-free: the only dependency between steps is
+    // the shuffle of lane r - 1's last result (the upper value; the upper-left one is
+    // the upper value of the step before)
     const int y = y0 + lane;
+    // EMR predicts on the top seven bits: the median of the values with the LSB
+    // cleared is twice the median of the seven-bit values
+    const uint32_t keep = seven ? 0xFEu : 0xFFu;
+    const uint32_t FMc = ~FM & 0xFFu;
     uint64_t lb = lab[0];
     for (int s = 0; s < cols + WAVE_ROWS - 1; s++) {
       const uint32_t bu = __shfl_up_sync(0xffffffffu, o1, 1);   // lane r-1: pixel (r-1, c)
-      const uint32_t cu = __shfl_up_sync(0xffffffffu, o0, 1);   // lane r-1: pixel (r-1, c-1)
       const int c = s - lane;
-      o0 = o1;
-      if (lane < rows && c >= 0 && c < cols) {
-        const int x = x0 + c;
-        const uint32_t D = T[lane * WAVE_PITCH + c];
-        const uint32_t label = (uint32_t)(lb & 1ull);
+      const bool act = lane < rows && c >= 0 && c < cols;
+      const int cc = c < 0 ? 0 : (c >= cols ? cols - 1 : c);
+      const uint32_t D = T[lane * WAVE_PITCH + cc];
+      const uint32_t Bv = lane > 0 ? bu : (uint32_t)U[1 + cc];
+      const uint32_t Cv = lane > 0 ? cprev : (uint32_t)U[cc];
+      cprev = bu;
+      const uint32_t a = o1 & keep, bb = Bv & keep, cv = Cv & keep;
+      const uint32_t mn = min(a, bb), mx = max(a, bb);
+      uint32_t pred = mn + mx - min(max(cv, mn), mx);          // MED = min + max - clamp(C)
+      pred = (x0 + c == 0) ? (Bv & keep) : pred;               // column 0: from above
+      pred = (y == 0) ? (o1 & keep) : pred;                     // row 0: from the left
+      const uint32_t out = (lb & 1ull) ? D : ((pred & FM) | (D & FMc));
+      if (act) {
+        T[lane * WAVE_PITCH + c] = (uint8_t)out;
+        o1 = out;
         if ((c & 63) == 63) {
           // next 64 labels: shift the words down (static register indices)
 #pragma unroll
@@ -128,24 +144,6 @@ __global__ void __launch_bounds__(32 * WAVE_WARPS) k_med_wave(Batch B) {
         } else {
           lb >>= 1;
         }
-        uint32_t out = D;
-        if (!label) {
-          const uint32_t A = o1;
-          const uint32_t Bv = lane > 0 ? bu : U[1 + c];
-          const uint32_t C = lane > 0 ? cu : U[c];
-          uint32_t pred;
-          if (y == 0) pred = seven ? (A & 0xFEu) : A;            // row 0: from the left
-          else if (x == 0) pred = seven ? (Bv & 0xFEu) : Bv;     // column 0: from above
-          else {
-            const uint32_t a = seven ? A >> 1 : A, bb = seven ? Bv >> 1 : Bv, cc = seven ? C >> 1 : C;
-            const uint32_t mx = max(a, bb), mn = min(a, bb);
-            const uint32_t m = cc >= mx ? mn : cc <= mn ? mx : a + bb - cc;
-            pred = seven ? m << 1 : m;
-          }
-          out = (pred & FM) | (D & ~FM & 0xFFu);
-        }
-        T[lane * WAVE_PITCH + c] = (uint8_t)out;
-        o1 = out;
       }
     }
     __syncwarp();
