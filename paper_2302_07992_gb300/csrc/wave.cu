@@ -13,6 +13,8 @@
 //     every tile a warp waits for was handed out earlier to a running warp.
 // Input: the de-rotated, decrypted image in dst (written by the gather pass) and the
 // de-rotated label bits in B.lab; output: dst, recovered in place.
+#include <type_traits>
+
 #include "../../include/rdhei.h"
 #include "common.cuh"
 
@@ -44,13 +46,16 @@ __device__ __forceinline__ uint64_t lab_row64(const Batch& B, const ImgDesc& d, 
 
 template <int WCOLS>
 __global__ void __launch_bounds__(32 * WAVE_WARPS) k_med_wave(Batch B) {
-  constexpr int WAVE_PITCH = WCOLS + 4;
+  // rows padded by WAVE_ROWS bytes on both sides, so that the lanes that have not
+  // started or have finished read in bounds without clamping their column
+  constexpr int PAD = WAVE_ROWS;
+  constexpr int WAVE_PITCH = WCOLS + 2 * PAD + 4;
   constexpr int NLAB = WCOLS / 64;                           // 64-pixel label words per row
   __shared__ __align__(16) uint8_t tiles[WAVE_WARPS][WAVE_ROWS * WAVE_PITCH];
-  __shared__ uint8_t uprow[WAVE_WARPS][WCOLS + 4];          // [0] = upper-left corner, [1 + c] = column c
+  __shared__ uint8_t uprow[WAVE_WARPS][WCOLS + 2 * PAD + 4];   // [PAD] = upper-left corner, [PAD + 1 + c] = column c
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* T = tiles[warp];
-  uint8_t* U = uprow[warp];
+  uint8_t* T = tiles[warp] + PAD;                            // T[r * WAVE_PITCH + c], c in [-PAD, WCOLS + PAD)
+  uint8_t* U = uprow[warp] + PAD;
   for (;;) {
     uint32_t k = 0;
     if (lane == 0) k = atomicAdd(B.tickets + 7, 1u);
@@ -111,41 +116,45 @@ __global__ void __launch_bounds__(32 * WAVE_WARPS) k_med_wave(Batch B) {
 
     // one pixel per lane and step, branch-free: the only dependency between steps is
     // the shuffle of lane r - 1's last result (the upper value; the upper-left one is
-    // the upper value of the step before)
+    // the upper value of the step before).  EMR predicts on the top seven bits: the
+    // median of the values with the LSB cleared is twice the median of the seven-bit
+    // values.  Tiles on the image's top row or left column also apply the border rules.
     const int y = y0 + lane;
-    // EMR predicts on the top seven bits: the median of the values with the LSB
-    // cleared is twice the median of the seven-bit values
     const uint32_t keep = seven ? 0xFEu : 0xFFu;
     const uint32_t FMc = ~FM & 0xFFu;
     uint64_t lb = lab[0];
-    for (int s = 0; s < cols + WAVE_ROWS - 1; s++) {
-      const uint32_t bu = __shfl_up_sync(0xffffffffu, o1, 1);   // lane r-1: pixel (r-1, c)
-      const int c = s - lane;
-      const bool act = lane < rows && c >= 0 && c < cols;
-      const int cc = c < 0 ? 0 : (c >= cols ? cols - 1 : c);
-      const uint32_t D = T[lane * WAVE_PITCH + cc];
-      const uint32_t Bv = lane > 0 ? bu : (uint32_t)U[1 + cc];
-      const uint32_t Cv = lane > 0 ? cprev : (uint32_t)U[cc];
-      cprev = bu;
-      const uint32_t a = o1 & keep, bb = Bv & keep, cv = Cv & keep;
-      const uint32_t mn = min(a, bb), mx = max(a, bb);
-      uint32_t pred = mn + mx - min(max(cv, mn), mx);          // MED = min + max - clamp(C)
-      pred = (x0 + c == 0) ? (Bv & keep) : pred;               // column 0: from above
-      pred = (y == 0) ? (o1 & keep) : pred;                     // row 0: from the left
-      const uint32_t out = (lb & 1ull) ? D : ((pred & FM) | (D & FMc));
-      if (act) {
-        T[lane * WAVE_PITCH + c] = (uint8_t)out;
-        o1 = out;
-        if ((c & 63) == 63) {
-          // next 64 labels: shift the words down (static register indices)
+    auto run = [&](auto border) {
+      for (int s = 0; s < cols + WAVE_ROWS - 1; s++) {
+        const uint32_t bu = __shfl_up_sync(0xffffffffu, o1, 1);   // lane r-1: pixel (r-1, c)
+        const int c = s - lane;                                    // in [-31, cols + 30]: padded
+        const uint32_t D = T[lane * WAVE_PITCH + c];
+        const uint32_t Bv = lane > 0 ? bu : (uint32_t)U[1 + c];
+        const uint32_t Cv = lane > 0 ? cprev : (uint32_t)U[c];
+        cprev = bu;
+        const uint32_t a = o1 & keep, bb = Bv & keep, cv = Cv & keep;
+        const uint32_t mn = min(a, bb), mx = max(a, bb);
+        uint32_t pred = mn + mx - min(max(cv, mn), mx);          // MED = min + max - clamp(C)
+        if (decltype(border)::value) {
+          pred = (x0 + c == 0) ? (Bv & keep) : pred;             // column 0: from above
+          pred = (y == 0) ? (o1 & keep) : pred;                   // row 0: from the left
+        }
+        const uint32_t out = (lb & 1ull) ? D : ((pred & FM) | (D & FMc));
+        if (lane < rows && c >= 0 && c < cols) {
+          T[lane * WAVE_PITCH + c] = (uint8_t)out;
+          o1 = out;
+          if ((c & 63) == 63) {
+            // next 64 labels: shift the words down (static register indices)
 #pragma unroll
-          for (int q = 0; q + 1 < NLAB; q++) lab[q] = lab[q + 1];
-          lb = lab[0];
-        } else {
-          lb >>= 1;
+            for (int q = 0; q + 1 < NLAB; q++) lab[q] = lab[q + 1];
+            lb = lab[0];
+          } else {
+            lb >>= 1;
+          }
         }
       }
-    }
+    };
+    if (ty == 0 || tx == 0) run(std::true_type{});
+    else run(std::false_type{});
     __syncwarp();
     if (words) {
       for (int r = 0; r < rows; r++)
