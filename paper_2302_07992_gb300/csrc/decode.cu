@@ -121,20 +121,29 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
       const uint4 v4 = *reinterpret_cast<const uint4*>(tout + row * TPITCH + 16 * quarter);
       const uint4 a4 = *reinterpret_cast<const uint4*>(aout + row * TPITCH + 16 * quarter);
       const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w}, aa[4] = {a4.x, a4.y, a4.z, a4.w};
+      uint32_t lw[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        if (lmr) {
+          lw[i] = (vv[i] >> 7) & 0x01010101u;
+          v[i] = (vv[i] & 0x7F7F7F7Fu) | (aa[i] << 7);            // bit 7 := eta
+        } else {
+          lw[i] = vv[i] & 0x01010101u;
+          v[i] = vv[i] ^ aa[i];                                   // LSB := map XOR s (decrypted LSB)
+        }
+      }
+      if (valid < 16) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const int nv = valid - 4 * i;                           // pixels past the row end: label 0
+          lw[i] &= nv <= 0 ? 0u : nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
+        }
+      }
+      if (x == 0 && valid > 0 && !med) lw[0] |= 1u;              // first image column: non-redundant
       uint32_t carry = 0, carried = 0;
 #pragma unroll
       for (int i = 0; i < 4; i++) {
-        uint32_t lab;
-        if (lmr) {
-          lab = (vv[i] >> 7) & 0x01010101u;
-          v[i] = (vv[i] & 0x7F7F7F7Fu) | (aa[i] << 7);            // bit 7 := eta
-        } else {
-          lab = vv[i] & 0x01010101u;
-          v[i] = vv[i] ^ aa[i];                                   // LSB := map XOR s (decrypted LSB)
-        }
-        const int nv = valid - 4 * i;                             // pixels past the row end: label 0
-        lab &= nv <= 0 ? 0u : nv >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nv)) - 1u);
-        if (i == 0 && x == 0 && valid > 0 && !med) lab |= 1u;     // first image column: non-redundant
+        const uint32_t lab = lw[i];
         if (ANY_MED) labs[i] = lab;
         uint32_t m = lab * 0xFFu;
         uint32_t f = v[i] & FM4 & m;
