@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
   // source tile of output tile (qty, tx): its angle sum above level 6, my 16 bytes of
   // it, the byte left of my row (quarter 0) and one subtree word (t < 88)
   uint32_t nP = 0, nU = 0, nw[4], nhalo = 0, nsub = 0;
+  uint32_t nup[4] = {0u, 0u, 0u, 0u}, ncorner = 0;              // MED: the row above the source tile
   auto fetch = [&](uint32_t tx) {
     const TileMap tm = B.tilemap[d.tile_base + qty * tiles_x + tx];
     nP = tm.enc_src;
@@ -166,6 +167,27 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
     if (quarter == 0 && y < H) nhalo = px0 > 0 ? __ldg(d.src + (size_t)y * W + px0 - 1) : ((nw[0] & 0xFFu) ^ 0xFFu);
     if (t < SUBTREE_BYTES / 4)
       nsub = __ldg(reinterpret_cast<const uint32_t*>(B.subtree + (size_t)(d.tile_base + nP) * SUBTREE_BYTES) + t);
+    if (ANY_MED && med && row == 0) {
+      // the row above the tile and its upper-left corner, for the MED prediction
+      const int uy = py0 - 1;
+      int uv = uy >= 0 ? min(16, W - x) : 0;
+      if (uv < 0) uv = 0;
+      const uint8_t* up = d.src + (size_t)(uy >= 0 ? uy : 0) * W + x;
+      if (uv == 16 && ((reinterpret_cast<uintptr_t>(up) & 15) == 0)) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(up));
+        nup[0] = v.x; nup[1] = v.y; nup[2] = v.z; nup[3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (4 * i + k < uv) v |= (uint32_t)__ldg(up + 4 * i + k) << (8 * k);
+          nup[i] = v;
+        }
+      }
+      if (quarter == 0) ncorner = (uy >= 0 && px0 > 0) ? __ldg(d.src + (size_t)uy * W + px0 - 1) : 0u;
+    }
   };
   fetch(tx0);
 
@@ -179,13 +201,9 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
     *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) = make_uint4(w[0], w[1], w[2], w[3]);
     if (quarter == 0) halo[row] = (uint8_t)nhalo;
     if (t < SUBTREE_BYTES / 4) reinterpret_cast<uint32_t*>(sub)[t] = nsub;
-    if (med && row == 0) {
-      // the row above the tile (and its upper-left corner) for the MED prediction
-      const int uy = py0 - 1, x = px0 + 16 * quarter;
-#pragma unroll
-      for (int k = 0; k < 16; k++)
-        uprow[16 * quarter + k] = (uy >= 0 && x + k < W) ? __ldg(d.src + (size_t)uy * W + x + k) : (uint8_t)0;
-      if (quarter == 0) uprow[TILE] = (uy >= 0 && px0 > 0) ? __ldg(d.src + (size_t)uy * W + px0 - 1) : (uint8_t)0;
+    if (ANY_MED && med && row == 0) {
+      *reinterpret_cast<uint4*>(uprow + 16 * quarter) = make_uint4(nup[0], nup[1], nup[2], nup[3]);
+      if (quarter == 0) uprow[TILE] = (uint8_t)ncorner;
     }
     if (tx + 1 < tx1) fetch(tx + 1);            // in flight while this tile is processed
     __syncthreads();
