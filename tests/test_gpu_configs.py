@@ -219,3 +219,62 @@ def test_overlapped_host_pipeline_matches_the_oracle():
             o = op.pay_off[k]
             assert np.array_equal(h_bits[o:o + nb].numpy(), pays[k][:nb]), k
     assert op.status() == 0
+
+
+def test_repeated_steps_without_host_synchronisation(rd):
+    """Three full steps (label_encrypt, embed, extract, decrypt_recover) queued back to
+    back on one stream over the same buffers, with no host synchronisation in between:
+    the kernels of an operation and of consecutive operations overlap programmatically,
+    and every read-after-write and write-after-read across them must still hold.  The
+    final outputs equal the oracle's."""
+    shapes = [(512, 512), (100, 130), (257, 333), (64, 1000)]
+    variants = [rd.EMR, rd.LMR, rd.EMR_MED, rd.LMR]
+    imgs = [synth.synth_image(H, W, 900 + i) for i, (H, W) in enumerate(shapes)]
+    seeds = [900 + i for i in range(len(shapes))]
+    n = len(imgs)
+    P = [rd.Params(variant=v, **_keys(s)) for v, s in zip(variants, seeds)]
+    d_img = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    enc = [torch.empty_like(x) for x in d_img]
+    marked = [torch.empty_like(x) for x in d_img]
+    rec = [torch.empty_like(x) for x in d_img]
+    N = [im.size for im in imgs]
+    lmr = [(v & 1) == rd.LMR for v in variants]
+    maps = [rd.bitbuf(N[i]) for i in range(n)]
+    etas = [rd.bitbuf(N[i]) for i in range(n)]
+    info = rd.new_info(n)
+    st = torch.cuda.current_stream()
+    p_enc = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=d_img[i], dst=enc[i], map_bits=maps[i],
+                                 eta_bits=etas[i] if lmr[i] else None, info=info[i]) for i in range(n)], st)
+    p_enc.run(rd.OP_LABEL_ENCRYPT, st)
+    torch.cuda.synchronize()
+    caps = [r["capacity"] for r in rd.read_info(info)]
+    pays = [synth.payload_bits(seeds[i], caps[i]) for i in range(n)]
+    d_pay = [rd.as_bitbuf(torch.from_numpy(pays[i]), caps[i]) for i in range(n)]
+    bits = [rd.bitbuf(caps[i]) for i in range(n)]
+    lm = [maps[i] if lmr[i] else None for i in range(n)]
+    p_emb = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=enc[i], dst=marked[i], map_bits=lm[i], payload=d_pay[i],
+                                 nbits=caps[i], info=info[i], b=0) for i in range(n)], st)
+    p_ext = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=marked[i], map_bits=lm[i], bits_out=bits[i],
+                                 max_bits=caps[i], info=info[i], b=0) for i in range(n)], st)
+    p_dec = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=marked[i], dst=rec[i], map_bits=lm[i],
+                                 eta_bits=etas[i] if lmr[i] else None, info=info[i], b=0) for i in range(n)], st)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for pl, op in ((p_enc, rd.OP_LABEL_ENCRYPT), (p_emb, rd.OP_EMBED), (p_ext, rd.OP_EXTRACT),
+                       (p_dec, rd.OP_DECRYPT_RECOVER)):
+            pl.run(op, st)
+    torch.cuda.synchronize()
+    for pl in (p_enc, p_emb, p_ext, p_dec):
+        assert pl.status(st) == 0
+    for i in range(n):
+        op = oracle.Params(variant=variants[i], **_keys(seeds[i]))
+        r = oracle.label_encrypt(op, imgs[i])
+        assert np.array_equal(enc[i].cpu().numpy(), r.enc), i
+        l_np = r.map_bits if lmr[i] else None
+        mref, _ = oracle.embed(op, r.b, r.enc, pays[i], r.capacity, l_np)
+        assert np.array_equal(marked[i].cpu().numpy(), mref), i
+        xref, xk = oracle.extract(op, r.b, mref, r.capacity, l_np)
+        assert np.array_equal(_bits(bits[i], xk), xref), i
+        rref = oracle.decrypt_recover(op, r.b, mref, l_np, r.eta_bits if lmr[i] else None)
+        assert np.array_equal(rec[i].cpu().numpy(), rref), i
+
