@@ -370,6 +370,7 @@ def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_n
     px = n * H * W
     # what came back is the verified result: recovered pixels as on the device path,
     # extracted bits equal to the payload
+    op_chunks = op.chunks
     assert torch.equal(h_rec, rec_ref.cpu()), "e2e recovered images differ"
     for k in range(n):
         nb = (caps[k] + 7) // 8
@@ -377,9 +378,52 @@ def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_n
         assert torch.equal(h_bits[o:o + nb], h_pay[o:o + nb]), f"e2e payload round trip, image {k}"
     h2d = h_img.numel() + op.pay_bytes + op.side_bytes
     d2h = h_rec.numel() + op.pay_bytes
-    return {"value": job_throughput(px, world, K, ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": K, "chunks": len(op.chunks),
-            "note": "pinned host buffers; copies of each chunk overlap the kernels of the neighbouring chunks"}
+    del op, h_img, h_pay, h_side, h_rec, h_bits
+    floor = copy_floor(torch, dev, int(h2d), int(d2h))
+    floor["mpx"] = px / (floor["both_ms"] * 1e-3) / 1e6
+    value = job_throughput(px, world, K, ms)
+    floor["frac"] = value / (floor["mpx"] * world)
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": K, "chunks": len(op_chunks),
+            "copy_floor": floor,
+            "note": "pinned host buffers; copies of each chunk overlap the kernels of the neighbouring chunks; "
+                    "copy_floor: one step's bytes as two single pinned copies, up and down at once, on this "
+                    "GPU's host link (best of 3), the time no overlap can beat"}
+
+
+def copy_floor(torch, dev, h2d: int, d2h: int, reps: int = 3) -> dict:
+    """Pinned host<->device copy bandwidth of this GPU for one step's bytes: each
+    direction alone and both at once on two streams (the pipeline overlaps them)."""
+    hu = torch.empty(h2d, dtype=torch.uint8, pin_memory=True)
+    hd = torch.empty(d2h, dtype=torch.uint8, pin_memory=True)
+    du = torch.empty(h2d, dtype=torch.uint8, device=dev)
+    dd = torch.empty(d2h, dtype=torch.uint8, device=dev)
+    s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(up: bool, down: bool) -> float:
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(s_up)
+            s_down.wait_event(ev[0])
+            if up:
+                with torch.cuda.stream(s_up):
+                    du.copy_(hu, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s_down):
+                    hd.copy_(dd, non_blocking=True)
+            ev[1].record(s_down)
+            s_up.wait_event(ev[1])
+            ev[2].record(s_up)
+            torch.cuda.synchronize(dev)
+            best = min(best, ev[0].elapsed_time(ev[2]))
+        return best
+
+    up_ms, down_ms, both_ms = timed(True, False), timed(False, True), timed(True, True)
+    del hu, hd, du, dd
+    return {"h2d_gbs": h2d / (up_ms * 1e-3) / 1e9, "d2h_gbs": d2h / (down_ms * 1e-3) / 1e9,
+            "both_gbs": (h2d + d2h) / (both_ms * 1e-3) / 1e9, "both_ms": both_ms}
 
 
 def verify_batch(args, rd, imgs, enc, marked, rec, maps, etas, payload, bits_out, info, caps, variants, params,
