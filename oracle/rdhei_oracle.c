@@ -11,7 +11,7 @@
  * Every routine follows the paper's own step order and notation:
  *   - keystream s / z2 .......... Sec. III-A-1 "Secret key generation"; the paper
  *                                 asks for any cryptographically secure stream
- *                                 cipher; this build fixes ChaCha20 (RFC 8439).
+ *                                 cipher; ChaCha20 (RFC 8439) is the one used here.
  *   - location maps ............. Sec. III-A-1a, Eqs. (gliding1), (gliding2)
  *   - choice of b ............... Eq. (optimal_b); LMR range b in [2,8] (Sec. III-B)
  *   - first MSB map eta ......... Eq. (MSB_map)
