@@ -333,8 +333,8 @@ def run_gpu(args, rank, world, local_rank):
     return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "K_breakdown": K2,
             "dominant": dom, "dominant_ms": dom_ms, "px_step": px_step,
             # kernels per step: one per stage, plus the zero-region clear of every
-            # operation's first stage and the offsets kernel of the two count stages
-            "kernels_per_step": sum(1 + (s_ == 0) + (nm in ("embed_count", "extract_count"))
+            # operation's first stage and the offsets kernel of the extractor's count stage
+            "kernels_per_step": sum(1 + (s_ == 0) + (nm == "extract_count")
                                     for _, _, s_, nm in stage_list),
             "verify": verify, "e2e": e2e, "clocks": clocks, "stage_list": [x[3] for x in stage_list],
             "caps": caps, "variants": variants, "tuning": tuning}
@@ -867,8 +867,9 @@ def roofline(res, peaks, args):
     hbm_bytes = {
         "pass1_keystream_hist": 1.0 * px,              # read I
         "enc_gather": 2.0 * px,                        # read I (gathered), write I_e
-        "z2_encrypt": 2 * der / 8 * px,                # read message, write K2-encrypted message
-        "embed_count": 0.5 * px,                       # read the map (EMR: LSB plane; LMR: packed map)
+        # read message, write K2-encrypted message; read the map (EMR: LSB plane; LMR: packed map)
+        "z2_encrypt_count": 2 * der / 8 * px + 0.5 * px,
+        "embed_offsets": 0.0,
         "embed_scan": (2.0 + der / 8) * px,            # read I_e + encrypted message, write I_e'
         "extract_count": 0.5 * px,
         "extract_scan": (1.0 + der / 8) * px,          # read I_e', write raw slot bits
@@ -882,7 +883,7 @@ def roofline(res, peaks, args):
         hbm_bytes["dec_gather_recover"] = 0.0
         hbm_bytes["med_wavefront"] = 1.0 * px
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
-                "z2_encrypt": der / 8 * px, "z2_decrypt": der / 8 * px}
+                "z2_encrypt_count": der / 8 * px, "z2_decrypt": der / 8 * px}
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SMS * ALU_LANES_PER_SM * clock_mhz * 1e6           # ALU-pipe ops/s
     hbm_peak = peaks.get("hbm_gbs", 6777.0)

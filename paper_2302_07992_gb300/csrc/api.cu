@@ -15,6 +15,8 @@ void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t s
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 void launch_count(const Batch& B, bool extract, cudaStream_t st);
+void launch_offsets(const Batch& B, bool extract, cudaStream_t st);
+void launch_z2_count(const Batch& B, cudaStream_t st);
 void launch_scan(const Batch& B, bool extract, cudaStream_t st);
 void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st);
 void launch_lmr_side(const Batch& B, cudaStream_t st);
@@ -365,7 +367,8 @@ const char* rdhei_stage_name(int op, int stage) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
     case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 4 ? dec[stage] : "";
-    case RDHEI_OP_EMBED: return stage == 0 ? "z2_encrypt" : stage == 1 ? "embed_count" : stage == 2 ? "embed_scan" : "";
+    case RDHEI_OP_EMBED:
+      return stage == 0 ? "z2_encrypt_count" : stage == 1 ? "embed_offsets" : stage == 2 ? "embed_scan" : "";
     case RDHEI_OP_EXTRACT:
       return stage == 0 ? "extract_count" : stage == 1 ? "extract_scan" : stage == 2 ? "z2_decrypt" : "";
     case RDHEI_OP_LMR_SET_SIDE: return stage == 0 ? "lmr_side" : "";
@@ -403,8 +406,8 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       else launch_enc_pass2(B, p->any_lmr, p->any_med, st);
       break;
     case RDHEI_OP_EMBED:
-      if (stage == 0) launch_z2_xor(B, false, st);
-      else if (stage == 1) launch_count(B, false, st);
+      if (stage == 0) launch_z2_count(B, st);
+      else if (stage == 1) launch_offsets(B, false, st);
       else launch_scan(B, false, st);
       break;
     case RDHEI_OP_EXTRACT:

@@ -3,14 +3,15 @@
 // rotated image, hold the K2-encrypted message back to back.
 //
 // Both sides are split the way the paper describes them:
-//   hider:    encrypt the message with K2 (k_z2_xor: e = m XOR z2, one ChaCha20 block
-//             per thread over the message), then write e into the slots (k_scan);
+//   hider:    encrypt the message with K2 (e = m XOR z2, one ChaCha20 block per
+//             thread over the message), then write e into the slots (k_scan);
 //   receiver: concatenate the slots (k_scan), then decrypt with K2 (k_z2_xor).
 // A pixel's first slot index is an exclusive prefix sum of slots over the raster.
-// The scan is reduce-then-scan over chunks of 8192 pixels: k_count counts each
-// chunk's slots and the last CTA of an image turns the counts into offsets; k_scan
-// then writes (hider) or gathers (receiver) each chunk's slots at its offset.  No CTA
-// ever waits for another.
+// The scan is reduce-then-scan over chunks of 8192 pixels: the count pass counts each
+// chunk's slots, k_offsets (one CTA per image) turns the counts into offsets, and
+// k_scan writes (hider) or gathers (receiver) each chunk's slots at its offset.  The
+// hider's encryption and count pass share one grid (k_z2_count); the receiver's count
+// pass is k_count.  No CTA ever waits for another.
 #include "common.cuh"
 #include "../../include/rdhei.h"
 
@@ -160,11 +161,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 // block-level synchronisation, no chunk-to-chunk dependency).  EMR counts the pixels
 // whose LSB (the location-map bit) is 0, LMR the 0 bits of the packed map.
 constexpr int COUNT_WARPS = 8;
-__global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) {
+__device__ __forceinline__ void count_chunks(const Batch& B, uint32_t cta) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   const int lane = threadIdx.x & 31;
-  const uint32_t g = blockIdx.x * COUNT_WARPS + (threadIdx.x >> 5);
+  const uint32_t g = cta * COUNT_WARPS + (threadIdx.x >> 5);
   if (g >= B.total_chunks) return;
   const int img = owner_of(B.chunk_prefix, B.n_images, g);
   const ImgDesc& d = B.desc[img];
@@ -214,6 +215,7 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) {
   z = __reduce_add_sync(0xffffffffu, z);
   if (lane == 0) reinterpret_cast<uint32_t*>(B.chunk_status)[g] = z * (uint32_t)slots_of(d, info);
 }
+__global__ void __launch_bounds__(32 * COUNT_WARPS) k_count(Batch B) { count_chunks(B, blockIdx.x); }
 
 // Per image: exclusive prefix of the chunk counts (the bit offset at which each chunk's
 // slots start -- Sec. III-A-2's "concatenation" order), the image totals and, for the
@@ -481,8 +483,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
 //   decrypt (receiver):  out[w] ^= z2[w] for the extracted bits, zero past `extracted`.
 // Words are the stream's bytes read little-endian, so the XOR is byte-wise.
 template <bool DECRYPT>
-__global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
-  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;   // global block index
+__device__ __forceinline__ void z2_block(const Batch& B, uint32_t j) {   // j: global block index
   if (j >= B.total_z2_blocks) return;
   const int img = owner_of(B.z2_prefix, B.n_images, j);
   const ImgDesc& d = B.desc[img];
@@ -523,6 +524,22 @@ __global__ void __launch_bounds__(128) k_z2_xor(Batch B) {
     out[nwords - 1] &= bswap32(0xFFFFFFFFu << (32 - keep));
   }
 }
+template <bool DECRYPT>
+__global__ void __launch_bounds__(128) k_z2_xor(Batch B) { z2_block<DECRYPT>(B, blockIdx.x * blockDim.x + threadIdx.x); }
+
+// The hider's first kernel: the K2 encryption of the message and the slot count of
+// every chunk, in one grid.  The two are independent of each other; the count is
+// bound by its reads of the image and the encryption by ChaCha20's integer work, so
+// their CTAs alternate (even blocks count, odd blocks encrypt, while both have work
+// left) and share the SMs instead of running one after the other.
+constexpr int Z2C_THREADS = 32 * COUNT_WARPS;
+__global__ void __launch_bounds__(Z2C_THREADS) k_z2_count(Batch B, uint32_t count_ctas, uint32_t z2_ctas) {
+  const uint32_t both = 2 * min(count_ctas, z2_ctas), b = blockIdx.x;
+  const bool count = b < both ? (b & 1u) == 0 : count_ctas > z2_ctas;
+  const uint32_t i = b < both ? b >> 1 : b - both / 2;
+  if (count) count_chunks(B, i);
+  else z2_block<false>(B, i * Z2C_THREADS + threadIdx.x);
+}
 
 // LMR side information into bit 7 (Sec. III-B-1): pixel q < side_nbits.
 __global__ void k_lmr_side(Batch B) {
@@ -550,11 +567,23 @@ static int persistent_grid(K kernel, uint32_t work) {
   return (int)(work < g ? work : g);
 }
 // count + per-image offsets
+void launch_offsets(const Batch& B, bool extract, cudaStream_t st);
 void launch_count(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
   launch_pdl(k_count, dim3((B.total_chunks + COUNT_WARPS - 1) / COUNT_WARPS), dim3(32 * COUNT_WARPS), 0, st, B);
+  launch_offsets(B, extract, st);
+}
+void launch_offsets(const Batch& B, bool extract, cudaStream_t st) {
+  if (B.total_chunks == 0) return;
   if (extract) launch_pdl(k_offsets<true>, dim3(B.n_images), dim3(HIDE_THREADS), 0, st, B);
   else launch_pdl(k_offsets<false>, dim3(B.n_images), dim3(HIDE_THREADS), 0, st, B);
+}
+// hider: message encryption and slot counts in one grid (the offsets follow)
+void launch_z2_count(const Batch& B, cudaStream_t st) {
+  const uint32_t cc = (B.total_chunks + COUNT_WARPS - 1) / COUNT_WARPS;
+  const uint32_t zc = (B.total_z2_blocks + Z2C_THREADS - 1) / Z2C_THREADS;
+  if (cc + zc == 0) return;
+  launch_pdl(k_z2_count, dim3(cc + zc), dim3(Z2C_THREADS), 0, st, B, cc, zc);
 }
 void launch_scan(const Batch& B, bool extract, cudaStream_t st) {
   if (B.total_chunks == 0) return;
