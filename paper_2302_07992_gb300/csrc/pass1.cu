@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
     }
     // per-row zero counts = valid pixels - nonzero ones; reduce over the CTA
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      // the 64 examined bytes include the padding past the row end, all "differs"
-      uint32_t z = (GENERAL || len > 0) ? 64u - (nz[k] >> 7) : 0u;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-      if (lane == 0) zero_cnt[warp][k] = z;
+    for (int k = 0; k < 8; k += 2) {
+      // the 64 examined bytes include the padding past the row end, all "differs";
+      // two counts (<= 64 a row, <= 2048 a warp) in the halves of one word
+      const uint32_t z0 = (GENERAL || len > 0) ? 64u - (nz[k] >> 7) : 0u;
+      const uint32_t z1 = (GENERAL || len > 0) ? 64u - (nz[k + 1] >> 7) : 0u;
+      const uint32_t z = __reduce_add_sync(0xffffffffu, z0 | (z1 << 16));
+      if (lane == 0) { zero_cnt[warp][k] = z & 0xFFFFu; zero_cnt[warp][k + 1] = z >> 16; }
     }
   } else {
     // K1 receiver: decrypt into the stash, keep the map bit, and record the aux plane
