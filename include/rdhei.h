@@ -174,7 +174,8 @@ int rdhei_plan_run(rdhei_plan *plan, int op, void *stream);
 void rdhei_plan_destroy(rdhei_plan *plan);
 
 /* The kernels of one operation, one launch per stage, for timing each kernel with
- * events recorded between stages: stage 0 also issues the per-call workspace memsets.
+ * events recorded between stages: stage 0 also clears the per-call region of the
+ * workspace (one kernel, or a memset when that region is not 16-byte aligned).
  * rdhei_plan_run(plan, op) == every stage of op in order.  Unknown op: 0 stages.
  * rdhei_plan_stage_active: 1 when the stage launches work for this plan's jobs (the
  * MED wavefront stage of rdhei_decrypt_recover launches only for MED variants). */
