@@ -978,6 +978,67 @@ def measured_traffic(kernel: str, px_per_launch: int):
     return None if k is None else k["dram_bytes_per_px"] * px_per_launch
 
 
+# ncu kernel name -> stage name, for the kernels of the traffic capture
+TRAFFIC_KERNELS = {"k_pass1<0, 0, 0>": "pass1_keystream_hist", "k_enc_rows<1, 0>": "enc_gather",
+                   "k_scan<0>": "embed_scan", "k_scan<1>": "extract_scan",
+                   "k_pass1<1, 0, 0>": "pass1_keystream_decrypt", "k_dec_strip<1, 0>": "dec_gather_recover"}
+TRAFFIC_CAPTURE = ('ncu --set full --clock-control none -k regex:"k_pass1|k_enc_rows|k_scan|k_dec_strip" -c 8 '
+                   '-o prof_full600 python bench.py --images 600 --steps 3 --warmup 3 --no-cpu-baseline')
+
+
+def traffic_from_csv(csv_path: str, out_path: str, images: int = 600, size: int = 512) -> dict:
+    """Per-pixel DRAM traffic and pipe counters of the captured kernels, from the raw page
+    of an ncu report (`ncu -i prof_full600.ncu-rep --page raw --csv > raw.csv`) of
+    TRAFFIC_CAPTURE, written with the current kernel source hash."""
+    import csv
+    with open(csv_path) as f:
+        rows = list(csv.reader(f))
+    head, units, data = rows[0], rows[1], rows[2:]
+    col = {name: i for i, name in enumerate(head)}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "ms": 1e3}
+
+    def num(r, metric):
+        return float(r[col[metric]]) * scale.get(units[col[metric]], 1.0)
+
+    def short(name):
+        name = name.replace("void ", "")
+        return name[:name.index("(")] if "(" in name else name
+
+    px = images * size * size
+    groups = {}
+    for r in data:
+        stage = TRAFFIC_KERNELS.get(short(r[col["Kernel Name"]]))
+        if stage is not None:
+            groups.setdefault(stage, []).append(r)
+    kernels = {}
+    for stage, rs in groups.items():
+        n = len(rs)
+        rd_b = sum(num(r, "dram__bytes_read.sum") for r in rs) / n
+        wr_b = sum(num(r, "dram__bytes_write.sum") for r in rs) / n
+        first = rs[0]
+        kernels[stage] = {
+            "kernel": short(first[col["Kernel Name"]]), "launches_captured": n,
+            "dram_bytes_per_px": (rd_b + wr_b) / px, "read_per_px": rd_b / px, "write_per_px": wr_b / px,
+            "us_600": sum(num(r, "gpu__time_duration.sum") for r in rs) / n,
+            "alu_pipe_pct": num(first, "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
+            "fma_pipe_pct": num(first, "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"),
+            "issue_pct": num(first, "sm__issue_active.avg.pct_of_peak_sustained_elapsed"),
+            "dram_pct": num(first, "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+            "warps_active_pct": num(first, "sm__warps_active.avg.pct_of_peak_sustained_active"),
+            "regs": int(num(first, "launch__registers_per_thread")),
+            "inst_per_px": num(first, "smsp__inst_executed.sum") / px,
+            "tensor_pipe_pct": num(first, "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")}
+    doc = {"about": f"DRAM traffic per pixel of each kernel from one `ncu --set full` capture of a {images}-image "
+                    f"{size}x{size} batch; bench.py scales it to its 1000-image launches (traffic grows with the "
+                    "pixel count: every kernel streams whole images) and reports it only while the sources of the "
+                    "timed path's kernels hash to source_hash. Written by `python bench.py --traffic-from raw.csv`.",
+           "source_hash": kernel_source_hash(), "command": TRAFFIC_CAPTURE, "pixels_per_launch": px,
+           "kernels": kernels}
+    with open(out_path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return doc
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1010,11 +1071,18 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4)
     ap.add_argument("--reference-budget", type=float, default=45.0,
                     help="--impl reference: seconds of oracle work over all its steps")
+    ap.add_argument("--traffic-from", metavar="RAW_CSV",
+                    help="write profiles/dram_traffic_batch600x512.json from the raw ncu page of the traffic "
+                         "capture and exit (no GPU needed)")
     ap.add_argument("--med", action="store_true",
                     help="the related-work MED predictor variants (EMR_MED / LMR_MED) instead of the paper's "
                          "glide; recovery runs as a tiled anti-diagonal wavefront")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.traffic_from:
+        doc = traffic_from_csv(args.traffic_from, os.path.join(ROOT, "profiles", "dram_traffic_batch600x512.json"))
+        print(json.dumps({k: round(v["dram_bytes_per_px"], 3) for k, v in doc["kernels"].items()}))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
