@@ -278,3 +278,72 @@ def test_repeated_steps_without_host_synchronisation(rd):
         rref = oracle.decrypt_recover(op, r.b, mref, l_np, r.eta_bits if lmr[i] else None)
         assert np.array_equal(rec[i].cpu().numpy(), rref), i
 
+
+
+def test_full_benchmark_batch_sampled(rd):
+    """The benchmark's own workload and launch configuration -- 1000 synthetic 512 x 512
+    images, EMR (even) / LMR (odd) with ceil(N/8) side bits, full-capacity payloads,
+    one plan per operation over the whole batch, jobs built as bench.py builds them --
+    and a sample of its images checked against the oracle output by output."""
+    import bench
+    n, H, W = 1000, 512, 512
+    N = H * W
+    imgs_np = bench.make_images(n, H, W)              # the benchmark's generator (a spawned pool)
+    variants = [rd.EMR if k % 2 == 0 else rd.LMR for k in range(n)]
+    lmr = [(v & 1) == rd.LMR for v in variants]
+    params = [rd.Params(variant=variants[k], **{f: bench.image_keys(k)[f] for f in ("k1", "nonce1", "k2", "nonce2")})
+              for k in range(n)]
+    imgs = torch.from_numpy(imgs_np).cuda()
+    enc, marked, rec = torch.empty_like(imgs), torch.empty_like(imgs), torch.empty_like(imgs)
+    mb = ((N + 31) // 32) * 4
+    maps = torch.zeros((n, mb), dtype=torch.uint8, device="cuda")
+    etas = torch.zeros((n, mb), dtype=torch.uint8, device="cuda")
+    sn = bench.side_nbits(H, W)
+    side_np = np.zeros((n, ((sn + 31) // 32) * 4), np.uint8)
+    for k in range(n):
+        if lmr[k]:
+            b = synth.random_bits(k, sn)
+            side_np[k, :b.size] = b
+    sides = torch.from_numpy(side_np).cuda()
+    info = rd.new_info(n)
+    rd.Plan([rd.make_job(params[k], H, W, src=imgs[k], dst=enc[k], map_bits=maps[k] if lmr[k] else None,
+                         eta_bits=etas[k] if lmr[k] else None, side_bits=sides[k] if lmr[k] else None,
+                         side_nbits=sn if lmr[k] else 0, info=info[k]) for k in range(n)]).run(rd.OP_LABEL_ENCRYPT)
+    torch.cuda.synchronize()
+    caps = [r["capacity"] for r in rd.read_info(info)]
+    pb = ((7 * N + 31) // 32) * 4
+    pay_np = np.zeros((n, pb), np.uint8)
+    for k in range(n):
+        b = synth.payload_bits(synth.image_seed(bench.BASE_SEED, k), caps[k])
+        pay_np[k, :b.size] = b
+    payload = torch.from_numpy(pay_np).cuda()
+    bits = torch.zeros((n, pb), dtype=torch.uint8, device="cuda")
+    m = [maps[k] if lmr[k] else None for k in range(n)]
+    rd.Plan([rd.make_job(params[k], H, W, src=enc[k], dst=marked[k], map_bits=m[k], payload=payload[k],
+                         nbits=caps[k], info=info[k], b=0) for k in range(n)]).run(rd.OP_EMBED)
+    rd.Plan([rd.make_job(params[k], H, W, src=marked[k], map_bits=m[k], bits_out=bits[k], max_bits=caps[k],
+                         info=info[k], b=0) for k in range(n)]).run(rd.OP_EXTRACT)
+    rd.Plan([rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], map_bits=m[k],
+                         eta_bits=etas[k] if lmr[k] else None, info=info[k], b=0)
+             for k in range(n)]).run(rd.OP_DECRYPT_RECOVER)
+    torch.cuda.synchronize()
+    got = rd.read_info(info)
+    sample = sorted({0, 1, 2, 3, 498, 499, 998, 999} | set(np.random.default_rng(7).integers(0, n, 8).tolist()))
+    for k in sample:
+        v = variants[k]
+        op = oracle.Params(variant=v, **{f: bench.image_keys(k)[f] for f in ("k1", "nonce1", "k2", "nonce2")})
+        side = synth.random_bits(k, sn) if lmr[k] else None
+        r = oracle.label_encrypt(op, imgs_np[k], side, sn if lmr[k] else 0)
+        g = got[k]
+        assert g["hist"] == [int(x) for x in r.hist] and g["b"] == r.b and g["capacity"] == r.capacity, k
+        assert np.array_equal(enc[k].cpu().numpy(), r.enc), k
+        lm = r.map_bits if lmr[k] else None
+        if lmr[k]:
+            assert np.array_equal(_bits(maps[k], N), r.map_bits), k
+            assert np.array_equal(_bits(etas[k], N), r.eta_bits), k
+        mref, emb = oracle.embed(op, r.b, r.enc, pay_np[k, :(r.capacity + 7) // 8], r.capacity, lm)
+        assert g["embedded"] == emb and np.array_equal(marked[k].cpu().numpy(), mref), k
+        xref, xk = oracle.extract(op, r.b, mref, r.capacity, lm)
+        assert g["extracted"] == xk and np.array_equal(_bits(bits[k], xk), xref), k
+        rref = oracle.decrypt_recover(op, r.b, mref, lm, r.eta_bits if lmr[k] else None)
+        assert np.array_equal(rec[k].cpu().numpy(), rref), k
