@@ -288,10 +288,26 @@ def run_gpu(args, rank, world, local_rank):
                      for k in range(n)]
         wave_cols, times = tune.best_wave_cols(tune_jobs, stream)
         tuning = {"wave_cols": wave_cols, "ms_per_width": times}
-    plan_emb, plan_ext = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream)
-    plan_dec = rd.Plan(dec_jobs, stream, wave_cols=wave_cols)
-    plans = [(plan_enc, rd.OP_LABEL_ENCRYPT), (plan_emb, rd.OP_EMBED), (plan_ext, rd.OP_EXTRACT),
-             (plan_dec, rd.OP_DECRYPT_RECOVER)]
+    if args.path == "fused":
+        # owner + hider in one call, the receiver with both keys in another
+        fenc_jobs, fdec_jobs = [], []
+        for k in range(n):
+            lmr = (variants[k] & 1) == rd.LMR
+            m = maps[k] if lmr else None
+            fenc_jobs.append(rd.make_job(params[k], H, W, src=imgs[k], dst=marked[k], map_bits=m,
+                                         eta_bits=etas[k] if lmr else None, side_bits=sides[k] if lmr else None,
+                                         side_nbits=sn if lmr else 0, payload=payload[k], nbits=caps[k],
+                                         info=info[k]))
+            fdec_jobs.append(rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], map_bits=m,
+                                         eta_bits=etas[k] if lmr else None, bits_out=bits_out[k],
+                                         max_bits=caps[k], info=info[k], b=0))
+        plans = [(rd.Plan(fenc_jobs, stream), rd.OP_ENCODE),
+                 (rd.Plan(fdec_jobs, stream, wave_cols=wave_cols), rd.OP_DECODE)]
+    else:
+        plan_emb, plan_ext = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream)
+        plan_dec = rd.Plan(dec_jobs, stream, wave_cols=wave_cols)
+        plans = [(plan_enc, rd.OP_LABEL_ENCRYPT), (plan_emb, rd.OP_EMBED), (plan_ext, rd.OP_EXTRACT),
+                 (plan_dec, rd.OP_DECRYPT_RECOVER)]
     stage_list = [(pl, op, s, f"{rd.stages(op)[s]}") for pl, op in plans for s in pl.active_stages(op)]
 
     def step(events=None):
@@ -912,13 +928,18 @@ def roofline(res, peaks, args):
         "pass1_keystream_decrypt": 1.0 * px,           # read I_e'
         "dec_gather_recover": 1.0 * px,                # write I'
         "topmap": 0.0,
+        # fused calls
+        "topmap_strips": 0.0,
+        "enc_gather_embed": (2.0 + der / 8) * px,      # read I (gathered) and the message, write I_e'
+        "extract_strips": (1.0 + der / 8) * px,        # read I_e', write the decrypted message
     }
     if getattr(args, "med", False):
         # MED: the gather pass only stages the de-rotated pixels; the wavefront writes I'
         hbm_bytes["dec_gather_recover"] = 0.0
         hbm_bytes["med_wavefront"] = 1.0 * px
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
-                "z2_encrypt_count": der / 8 * px, "z2_decrypt": der / 8 * px}
+                "z2_encrypt_count": der / 8 * px, "z2_decrypt": der / 8 * px,
+                "enc_gather_embed": der / 8 * px, "extract_strips": der / 8 * px}
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = SMS * ALU_LANES_PER_SM * clock_mhz * 1e6           # ALU-pipe ops/s
     hbm_peak = peaks.get("hbm_gbs", 6777.0)
@@ -1074,6 +1095,9 @@ def main():
     ap.add_argument("--traffic-from", metavar="RAW_CSV",
                     help="write profiles/dram_traffic_batch600x512.json from the raw ncu page of the traffic "
                          "capture and exit (no GPU needed)")
+    ap.add_argument("--path", default="fused", choices=["fused", "separable"],
+                    help="fused: rdhei_encode (owner + hider) and rdhei_decode (both keys), 9 kernels a step; "
+                         "separable: the four calls of the paper's parties, 17 kernels a step")
     ap.add_argument("--med", action="store_true",
                     help="the related-work MED predictor variants (EMR_MED / LMR_MED) instead of the paper's "
                          "glide; recovery runs as a tiled anti-diagonal wavefront")
@@ -1093,6 +1117,8 @@ def main():
                           + "label_encrypt + full-capacity embed + extract + decrypt_recover per step",
               "images_per_gpu": args.images, "H": args.size, "W": args.size,
               "keystream": "ChaCha20 (RFC 8439)", "parallelism": f"replicas x{args.gpus}",
+              "path": ("rdhei_encode + rdhei_decode (fused calls)" if args.path == "fused" else
+                       "rdhei_label_encrypt, rdhei_embed, rdhei_extract, rdhei_decrypt_recover"),
               "l2": "no flush: each step streams ~1.6 GB (inputs and outputs > 129 MB L2)"}
 
     if args.config in ("c3", "c4", "c5") and args.impl == "gb300":

@@ -9,6 +9,9 @@
  *   data hider     rdhei_embed            Sec. III-A-2 / III-B-2
  *   receiver (K2)  rdhei_extract          Sec. III-A-3 / III-B-3, "receiver has only K2"
  *   receiver (K1)  rdhei_decrypt_recover  Sec. III-A-3 / III-B-3, "receiver has only K1"
+ * Two fused calls run two parties back to back with fewer passes over memory:
+ *   owner + hider  rdhei_encode           Sec. III-A-1 then III-A-2 (III-B-1, III-B-2)
+ *   both keys      rdhei_decode           Sec. III-A-3 / III-B-3, "receiver has both keys"
  * Each works on a batch of images of any sizes (one image is a batch of one).
  *
  * Conventions shared by every call
@@ -148,6 +151,32 @@ int rdhei_decrypt_recover(const rdhei_job *jobs, int n, void *ws, size_t ws_byte
  * embedding"): pixel q < side_nbits gets bit 7 := side bit q.  In place on job.dst. */
 int rdhei_lmr_set_side(const rdhei_job *jobs, int n, void *ws, size_t ws_bytes, void *stream);
 
+/* Owner and hider in one call (Sec. III-A-1 followed by Sec. III-A-2; Sec. III-B-1
+ * followed by Sec. III-B-2): the result equals rdhei_label_encrypt followed by
+ * rdhei_embed with the b it chose, bit for bit, in three kernels instead of eight.  The
+ * payload slots of each 64-row strip of the rotated image start at a bit offset derived
+ * from per-tile label counts of the first pass, so each strip is encrypted and then
+ * filled with the K2-encrypted payload by one CTA while it is still in L2.
+ * Job fields: src = I, dst = I_e' (the marked image; must not alias src), payload /
+ * nbits, K1 and K2; LMR: map_bits is REQUIRED (the rotated map is written there and
+ * read back by the hider's half), eta_bits optional, side_bits / side_nbits as for
+ * rdhei_label_encrypt (the compressed maps must therefore be known before the call; an
+ * owner that compresses the maps it is computing uses the separable calls).
+ * Writes dst, map_bits / eta_bits, info->{hist, b, capacity, embedded}; a payload longer
+ * than the capacity embeds the capacity and sets info->status = RDHEI_ECAPACITY. */
+int rdhei_encode(const rdhei_job *jobs, int n, void *ws, size_t ws_bytes, void *stream);
+
+/* Receiver with both keys (Sec. III-A-3 / III-B-3, "the receiver has both keys"): the
+ * result equals rdhei_extract followed by rdhei_decrypt_recover, bit for bit.  The first
+ * pass (K1 keystream, decryption, rotation angles) also counts each tile's payload
+ * slots, so the extraction kernel starts every 64-row strip at its bit offset and
+ * decrypts with K2 as it writes -- no count pass and no separate K2 pass.
+ * Job fields: src = I_e', dst = I' (must not alias src), bits_out / max_bits, b (0 =
+ * info->b), K1 and K2; LMR: map_bits and eta_bits required.  Writes bits_out
+ * (min(max_bits, capacity) bits, the last partial word zero-filled), dst and
+ * info->extracted. */
+int rdhei_decode(const rdhei_job *jobs, int n, void *ws, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------------------------
  * Plans: the calls above re-validate, re-lay-out and re-upload the batch's
  * descriptors on every call (a host-synchronous copy).  A plan does that once:
@@ -164,7 +193,9 @@ enum rdhei_op {
     RDHEI_OP_EMBED = 1,
     RDHEI_OP_EXTRACT = 2,
     RDHEI_OP_DECRYPT_RECOVER = 3,
-    RDHEI_OP_LMR_SET_SIDE = 4
+    RDHEI_OP_LMR_SET_SIDE = 4,
+    RDHEI_OP_ENCODE = 5,
+    RDHEI_OP_DECODE = 6
 };
 typedef struct rdhei_plan rdhei_plan;
 int rdhei_plan_create(const rdhei_job *jobs, int n, rdhei_plan **plan);

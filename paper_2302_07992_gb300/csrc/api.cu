@@ -10,7 +10,9 @@
 
 namespace rdhei {
 void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStream_t st);
-void launch_topmap(const Batch& B, bool owner, cudaStream_t st);
+void launch_topmap(const Batch& B, bool owner, bool fused, cudaStream_t st);
+void launch_enc_fused(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
+void launch_extract_strips(const Batch& B, cudaStream_t st);
 void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
@@ -35,7 +37,8 @@ struct rdhei_plan {
   size_t off_err = 0, off_zero = 0, zero_bytes = 0, off_tickets = 0, off_hist = 0, off_chunk_status = 0,
          off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_strip_prefix = 0, off_tile_rows = 0,
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, off_wave_flags = 0, off_wave_list = 0,
-         off_lab = 0, off_tile_owner = 0, off_strip_owner = 0, total = 0;
+         off_lab = 0, off_tile_owner = 0, off_strip_owner = 0, off_tile_cnt = 0, off_strip_base = 0,
+         off_strip_tot = 0, total = 0;
   uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0, total_wave = 0;
   int wave_cols = WAVE_COLS_DEFAULT;
   bool any_lmr = false, general = false, any_med = false;
@@ -148,6 +151,12 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)p->total_tiles * sizeof(TileMap), 256);
   p->off_lab = off;
   if (p->any_med) off = align_up(off + (size_t)p->total_tiles * AUX_BYTES, 256);
+  p->off_tile_cnt = off;
+  off = align_up(off + (size_t)p->total_tiles * 16, 256);
+  p->off_strip_base = off;
+  off = align_up(off + (size_t)p->total_strips * 4, 256);
+  p->off_strip_tot = off;
+  off = align_up(off + (size_t)p->total_strips * 4, 256);
   p->stash_off.resize(n);
   p->ebuf_off.resize(n);
   for (int i = 0; i < n; i++) {
@@ -305,6 +314,9 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.wave_list = reinterpret_cast<const uint2*>(base + p->off_wave_list);
   B.total_wave = p->total_wave;
   B.wave_cols = p->wave_cols;
+  B.tile_cnt = reinterpret_cast<uint16_t*>(base + p->off_tile_cnt);
+  B.strip_base = reinterpret_cast<uint32_t*>(base + p->off_strip_base);
+  B.strip_tot = reinterpret_cast<uint32_t*>(base + p->off_strip_tot);
   return RDHEI_OK;
 }
 
@@ -335,6 +347,20 @@ static int check_op(const rdhei_plan* p, int op) {
         if (lmr && (!j.map_bits || !j.eta_bits || !aligned4(j.map_bits) || !aligned4(j.eta_bits)))
           return RDHEI_EINVAL;
         break;
+      case RDHEI_OP_ENCODE:
+        if (!j.src || !j.dst) return RDHEI_EINVAL;
+        if ((j.map_bits && !aligned4(j.map_bits)) || (j.eta_bits && !aligned4(j.eta_bits))) return RDHEI_EINVAL;
+        if (lmr && j.side_nbits && (!j.side_bits || !aligned4(j.side_bits))) return RDHEI_EINVAL;
+        if (lmr && !j.map_bits) return RDHEI_EINVAL;         // the hider's half reads the map back
+        if (j.nbits && (!j.payload || !aligned4(j.payload))) return RDHEI_EINVAL;
+        if (j.nbits >= (1ull << 30)) return RDHEI_EINVAL;
+        break;
+      case RDHEI_OP_DECODE:
+        if (!j.src || !j.dst) return RDHEI_EINVAL;
+        if (j.max_bits && (!j.bits_out || !aligned4(j.bits_out))) return RDHEI_EINVAL;
+        if (lmr && (!j.map_bits || !j.eta_bits || !aligned4(j.map_bits) || !aligned4(j.eta_bits)))
+          return RDHEI_EINVAL;
+        break;
       case RDHEI_OP_LMR_SET_SIDE:
         if (!j.dst) return RDHEI_EINVAL;
         if (j.side_nbits && (!j.side_bits || !aligned4(j.side_bits))) return RDHEI_EINVAL;
@@ -348,8 +374,11 @@ static int check_op(const rdhei_plan* p, int op) {
 
 int rdhei_plan_stage_count(int op) {
   switch (op) {
+    case RDHEI_OP_DECODE:
+      return 5;
     case RDHEI_OP_DECRYPT_RECOVER:
       return 4;
+    case RDHEI_OP_ENCODE:
     case RDHEI_OP_LABEL_ENCRYPT:
     case RDHEI_OP_EMBED:
     case RDHEI_OP_EXTRACT:
@@ -364,7 +393,12 @@ int rdhei_plan_stage_count(int op) {
 const char* rdhei_stage_name(int op, int stage) {
   static const char* enc[3] = {"pass1_keystream_hist", "topmap", "enc_gather"};
   static const char* dec[4] = {"pass1_keystream_decrypt", "topmap", "dec_gather_recover", "med_wavefront"};
+  static const char* fenc[3] = {"pass1_keystream_hist", "topmap_strips", "enc_gather_embed"};
+  static const char* fdec[5] = {"pass1_keystream_decrypt", "topmap_strips", "extract_strips", "dec_gather_recover",
+                                "med_wavefront"};
   switch (op) {
+    case RDHEI_OP_ENCODE: return stage >= 0 && stage < 3 ? fenc[stage] : "";
+    case RDHEI_OP_DECODE: return stage >= 0 && stage < 5 ? fdec[stage] : "";
     case RDHEI_OP_LABEL_ENCRYPT: return stage >= 0 && stage < 3 ? enc[stage] : "";
     case RDHEI_OP_DECRYPT_RECOVER: return stage >= 0 && stage < 4 ? dec[stage] : "";
     case RDHEI_OP_EMBED:
@@ -387,7 +421,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
     if (rc) return rc;
     uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
     if (launch_zero(base + p->off_zero, p->zero_bytes, st) != cudaSuccess) return RDHEI_ECUDA;
-    if (op == RDHEI_OP_LABEL_ENCRYPT) {
+    if (op == RDHEI_OP_LABEL_ENCRYPT || op == RDHEI_OP_ENCODE) {
       // packed-map outputs of images whose rows do not start on a 16-bit boundary are
       // OR-ed word by word and must start from zero
       for (const rdhei_job& j : p->jobs) {
@@ -402,7 +436,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
   switch (op) {
     case RDHEI_OP_LABEL_ENCRYPT:
       if (stage == 0) launch_pass1(B, 0, p->general, p->any_med, st);
-      else if (stage == 1) launch_topmap(B, true, st);
+      else if (stage == 1) launch_topmap(B, true, false, st);
       else launch_enc_pass2(B, p->any_lmr, p->any_med, st);
       break;
     case RDHEI_OP_EMBED:
@@ -417,7 +451,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       break;
     case RDHEI_OP_DECRYPT_RECOVER:
       if (stage == 0) launch_pass1(B, 1, p->general, false, st);
-      else if (stage == 1) launch_topmap(B, false, st);
+      else if (stage == 1) launch_topmap(B, false, false, st);
       else if (stage == 2) launch_dec_pass2(B, p->any_lmr, p->any_med, st);
       else if (p->any_med) {
         // the wavefront owns its ticket and done flags: clear them so the stage can rerun
@@ -430,6 +464,24 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
       break;
     case RDHEI_OP_LMR_SET_SIDE:
       launch_lmr_side(B, st);
+      break;
+    case RDHEI_OP_ENCODE:
+      if (stage == 0) launch_pass1(B, 0, p->general, p->any_med, st);
+      else if (stage == 1) launch_topmap(B, true, true, st);
+      else launch_enc_fused(B, p->any_lmr, p->any_med, st);
+      break;
+    case RDHEI_OP_DECODE:
+      if (stage == 0) launch_pass1(B, 1, p->general, false, st);
+      else if (stage == 1) launch_topmap(B, false, true, st);
+      else if (stage == 2) launch_extract_strips(B, st);
+      else if (stage == 3) launch_dec_pass2(B, p->any_lmr, p->any_med, st);
+      else if (p->any_med) {
+        uint8_t* base = reinterpret_cast<uint8_t*>(p->ws);
+        if (cudaMemsetAsync(base + p->off_wave_flags, 0, (size_t)p->total_wave * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(base + p->off_tickets + 7 * 4, 0, 4, st) != cudaSuccess)
+          return RDHEI_ECUDA;
+        launch_med_wave(B, st);
+      }
       break;
   }
   return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
@@ -446,6 +498,7 @@ int rdhei_plan_set_wave_cols(rdhei_plan* p, int cols) {
 int rdhei_plan_stage_active(const rdhei_plan* p, int op, int stage) {
   if (!p || stage < 0 || stage >= rdhei_plan_stage_count(op)) return 0;
   if (op == RDHEI_OP_DECRYPT_RECOVER && stage == 3) return p->any_med ? 1 : 0;
+  if (op == RDHEI_OP_DECODE && stage == 4) return p->any_med ? 1 : 0;
   return 1;
 }
 
@@ -456,6 +509,8 @@ static const char* op_range_name(int op) {
     case RDHEI_OP_EXTRACT: return "rdhei_extract";
     case RDHEI_OP_DECRYPT_RECOVER: return "rdhei_decrypt_recover";
     case RDHEI_OP_LMR_SET_SIDE: return "rdhei_lmr_set_side";
+    case RDHEI_OP_ENCODE: return "rdhei_encode";
+    case RDHEI_OP_DECODE: return "rdhei_decode";
   }
   return "rdhei_plan_run";
 }
@@ -505,6 +560,12 @@ int rdhei_decrypt_recover(const rdhei_job* jobs, int n, void* ws, size_t ws_byte
 }
 int rdhei_lmr_set_side(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
   return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_LMR_SET_SIDE);
+}
+int rdhei_encode(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_ENCODE);
+}
+int rdhei_decode(const rdhei_job* jobs, int n, void* ws, size_t ws_bytes, void* stream) {
+  return run_once(jobs, n, ws, ws_bytes, stream, RDHEI_OP_DECODE);
 }
 
 int rdhei_workspace_status(void* ws, void* stream, int32_t* code) {

@@ -7,8 +7,10 @@
 //     aligned 2^k tiles, so tile = unit of gather;
 //   * the keystream s (Sec. "Secret key generation") is ChaCha20 (RFC 8439), one
 //     64-byte block per 64-pixel tile row when W is a multiple of 64;
-//   * raster-order scans (payload offsets of Sec. III-A-2) use 4096-pixel chunks with
-//     a decoupled look-back.
+//   * raster-order scans (payload offsets of Sec. III-A-2) are reduce-then-scan over
+//     8192-pixel chunks (separable calls) or start from per-strip offsets that the
+//     top-level pass derives from per-tile label counts (fused calls); no kernel waits
+//     for another CTA on this path.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -126,6 +128,9 @@ struct Batch {
   const uint2* wave_list;         // MED decode: (image, ty << 16 | tx) in anti-diagonal order
   uint32_t total_wave;
   int32_t wave_cols;              // MED decode: 0 = row-band pipeline, else tile width (64, 128, 256)
+  uint16_t* tile_cnt;             // total_tiles * 8: label-0 pixels per tile (owner: b = 1..8; receiver: [0])
+  uint32_t* strip_base;           // total_strips: first payload bit of each 64-row strip (fused calls)
+  uint32_t* strip_tot;            // total_strips: payload bits of each strip (fused calls)
 };
 
 // MED recovery wavefront tile: 32 rows (one warp lane per row) x wave_cols columns.
@@ -289,6 +294,18 @@ __device__ __forceinline__ uint32_t stream_bits32(const uint8_t* s, uint64_t nwo
   uint32_t sh = (uint32_t)(pos & 31);
   uint32_t w0 = wi < nwords ? bswap32(__ldg(w + wi)) : 0u;
   uint32_t w1 = (sh && wi + 1 < nwords) ? bswap32(__ldg(w + wi + 1)) : 0u;
+  uint32_t msb = sh ? (w0 << sh) | (w1 >> (32 - sh)) : w0;
+  return __brev(msb);
+}
+
+// The same from a stream that the calling kernel itself wrote earlier (coherent
+// L2 loads: the read-only path may not be used for data written by the same kernel).
+__device__ __forceinline__ uint32_t stream_bits32_cg(const uint8_t* s, uint64_t nwords, uint64_t pos) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(s);
+  uint64_t wi = pos >> 5;
+  uint32_t sh = (uint32_t)(pos & 31);
+  uint32_t w0 = wi < nwords ? bswap32(__ldcg(w + wi)) : 0u;
+  uint32_t w1 = (sh && wi + 1 < nwords) ? bswap32(__ldcg(w + wi + 1)) : 0u;
   uint32_t msb = sh ? (w0 << sh) | (w1 >> (32 - sh)) : w0;
   return __brev(msb);
 }

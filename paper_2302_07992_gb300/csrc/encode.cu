@@ -1,8 +1,9 @@
 // encode.cu -- content owner's second half: top rotation levels + choice of b
 // (k_topmap) and the gather pass that labels, rotates, encrypts and embeds the map
-// (k_enc_pass2).
+// (k_enc_rows); and the fused owner-and-hider kernel (k_enc_fused) that goes on to
+// write the K2-encrypted payload into the strip it has just encrypted.
 #include "permute.cuh"
-#include "../../include/rdhei.h"
+#include "slots.cuh"
 
 namespace rdhei {
 
@@ -15,38 +16,60 @@ __device__ __forceinline__ int top_off(int H, int W, int L) {
   return off;
 }
 
+constexpr int MAX_STRIPS = 1024;   // 64-row strips of the tallest image (H <= 65536)
+
 // One CTA per image.
 //   owner:    histogram -> hist[9], b (Eq. optimal_b), capacity, into rdhei_info;
 //   both:     sums of the tile totals up the levels above 6 (Eq. roration) and, per
-//             tile, where the composed rotation sends it and the angle sum above 6.
-__global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
+//             tile, where the composed rotation sends it and the angle sum above 6;
+//   fused:    per 64-row strip of the rotated image, its payload bits (the label-0
+//             pixels of its tiles times the slots per pixel) and their exclusive
+//             prefix in raster order -- the bit at which the strip's slots start in the
+//             concatenation of Sec. III-A-2 / III-A-3.  The owner counts its rotated
+//             tiles through the tile map (a tile moves as a whole, and the in-tile
+//             rotation only permutes its pixels); the receiver's tiles are already in
+//             the rotated domain.  Owner: embedded = min(nbits, capacity); receiver:
+//             extracted = min(max_bits, capacity), and the output words that two strips
+//             share (and the last, partial one) are cleared for the extractor's ORs.
+__global__ void __launch_bounds__(256) k_topmap(Batch B, int owner, int fused) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   __shared__ uint8_t top[TOP_SMEM];
+  __shared__ uint32_t strip_acc[MAX_STRIPS];
+  __shared__ int s_b;
   const int img = blockIdx.x;
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W, n = d.nlev;
   rdhei_info* info = reinterpret_cast<rdhei_info*>(d.info);
+  const int lmr = d.variant == RDHEI_LMR;
 
-  if (owner && threadIdx.x == 0) {
-    uint32_t z[10];
-    const uint32_t N = (uint32_t)H * (uint32_t)W;
-    for (int k = 1; k <= 8; k++) z[k] = B.hist_acc[16 * img + k - 1];
-    z[0] = N; z[9] = 0;
-    for (int t = 0; t <= 8; t++) info->hist[t] = t < 8 ? z[t] - z[t + 1] : z[8];
-    const int lmr = d.variant == RDHEI_LMR;
-    int b = d.b;
-    if (b <= 0) {
-      uint64_t best = 0; b = 2;
-      for (int c = 2; c <= (lmr ? 8 : 7); c++) {
-        uint64_t cap = (uint64_t)(lmr ? c - 1 : c) * z[c];
-        if (c == 2 || cap > best) { best = cap; b = c; }
+  if (threadIdx.x == 0) {
+    if (owner) {
+      uint32_t z[10];
+      const uint32_t N = (uint32_t)H * (uint32_t)W;
+      for (int k = 1; k <= 8; k++) z[k] = B.hist_acc[16 * img + k - 1];
+      z[0] = N; z[9] = 0;
+      for (int t = 0; t <= 8; t++) info->hist[t] = t < 8 ? z[t] - z[t + 1] : z[8];
+      int b = d.b;
+      if (b <= 0) {
+        uint64_t best = 0; b = 2;
+        for (int c = 2; c <= (lmr ? 8 : 7); c++) {
+          uint64_t cap = (uint64_t)(lmr ? c - 1 : c) * z[c];
+          if (c == 2 || cap > best) { best = cap; b = c; }
+        }
       }
+      info->b = b;
+      info->capacity = (uint64_t)(lmr ? b - 1 : b) * z[b];
+      info->status = 0;
+      s_b = b;
+    } else {
+      s_b = d.b > 0 ? d.b : info->b;
     }
-    info->b = b;
-    info->capacity = (uint64_t)(lmr ? b - 1 : b) * z[b];
-    info->status = 0;
   }
+  if (fused)
+    for (uint32_t i = threadIdx.x; i < d.tiles_y; i += blockDim.x) strip_acc[i] = 0u;
+  __syncthreads();
+  const int b = s_b;
 
   // levels 7..n: sums of the 4 children (level 7 from the tile totals)
   for (int L = 7; L <= n; L++) {
@@ -86,6 +109,12 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
       qx = (qx & ~(1u << k)) | ((qb & 1u) << k);
     }
     const uint32_t q = qy * d.tiles_x + qx;
+    if (fused) {
+      // label-0 pixels of the rotated tile: the owner's source tile t lands on q, the
+      // receiver's tile t is already a rotated one
+      const uint32_t cnt = B.tile_cnt[8 * (size_t)(d.tile_base + t) + (owner ? b - 1 : 0)];
+      atomicAdd(&strip_acc[owner ? qy : ty], cnt);
+    }
     if (!RDHEI_IDX_OK(B.err, q < ntiles)) continue;
     const uint8_t shi = (uint8_t)(S & 3u);           // S_6
     B.tilemap[d.tile_base + t].dec_dst = q;
@@ -93,6 +122,52 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
     B.tilemap[d.tile_base + q].enc_src = t;
     B.tilemap[d.tile_base + q].enc_shi = shi;
   }
+  if (!fused) return;
+  __syncthreads();
+
+  // strips: payload bits and their exclusive prefix (one warp; <= 1024 strips, 32 per lane)
+  const uint32_t slots = (uint32_t)(lmr ? b - 1 : b);
+  const uint32_t ns = d.tiles_y, sbase = __ldg(B.strip_prefix + img);
+  if (threadIdx.x < 32) {
+    const uint32_t lane = threadIdx.x, per = (ns + 31) / 32;
+    const uint32_t i0 = lane * per, i1 = min(i0 + per, ns);
+    uint32_t sum = 0;
+    for (uint32_t i = i0; i < i1; i++) sum += strip_acc[i] * slots;
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += u;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    uint32_t run = inc - sum;
+    for (uint32_t i = i0; i < i1; i++) {
+      const uint32_t v = strip_acc[i] * slots;
+      B.strip_base[sbase + i] = run;
+      B.strip_tot[sbase + i] = v;
+      strip_acc[i] = run;                              // the strip's first bit, for the clearing below
+      run += v;
+    }
+    if (lane == 0) {
+      if (owner) {
+        info->embedded = umin64(d.nbits, total);
+        if (d.nbits > total) { info->status = ERR_CAPACITY; set_error(B.err, ERR_CAPACITY); }
+      } else {
+        info->extracted = umin64(d.max_bits, total);
+      }
+    }
+  }
+  if (owner) return;
+  __syncthreads();
+  // receiver: words of bits_out that two strips share, and the last partial word, start
+  // at zero (the extractor writes them with atomicOr)
+  const uint64_t E = info->extracted;
+  uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
+  for (uint32_t i = threadIdx.x + 1; i < ns; i += blockDim.x) {
+    const uint32_t G = strip_acc[i];
+    if (G < E && (G & 31u)) out[G >> 5] = 0u;
+  }
+  if (threadIdx.x == 0 && (E & 31u)) out[E >> 5] = 0u;
 }
 
 // ---------------------------------------------------------------------------------
@@ -108,20 +183,35 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner) {
 //      into bit 7, packed rotated maps.
 // ---------------------------------------------------------------------------------
 template <bool ANY_LMR, bool ANY_MED>
-__global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint32_t nsplit) {
-  pdl_wait();      // the previous kernel of the operation has finished
-  pdl_trigger();
-  __shared__ __align__(16) uint8_t tin[TILE * TPITCH];
-  __shared__ __align__(16) uint8_t tout[TILE * TPITCH];
-  __shared__ __align__(16) uint8_t lin[ANY_LMR ? TILE * TPITCH : 16];
-  __shared__ __align__(16) uint8_t lout[ANY_LMR ? TILE * TPITCH : 16];
-  __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
-  __shared__ uint32_t selt[16];
-  __shared__ uint8_t halo[TILE];
-  __shared__ __align__(16) uint8_t uprow[ANY_MED ? TILE + 16 : 16];   // MED: the row above P, its left corner
+struct EncSmem {
+  __align__(16) uint8_t tin[TILE * TPITCH];
+  __align__(16) uint8_t tout[TILE * TPITCH];
+  __align__(16) uint8_t lin[ANY_LMR ? TILE * TPITCH : 16];
+  __align__(16) uint8_t lout[ANY_LMR ? TILE * TPITCH : 16];
+  __align__(16) uint8_t sub[SUBTREE_BYTES];
+  uint32_t selt[16];
+  uint8_t halo[TILE];
+  __align__(16) uint8_t uprow[ANY_MED ? TILE + 16 : 16];   // MED: the row above P, its left corner
+};
+
+// Output tiles [tx0, tx1) of one output tile row (`piece` of `nsplit` pieces).  `pre`
+// runs once, while the loads of the first source tile are in flight.
+struct NoPre {
+  __device__ __forceinline__ void operator()() const {}
+};
+template <bool ANY_LMR, bool ANY_MED, typename Pre = NoPre>
+__device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, uint32_t nsplit, uint32_t piece,
+                                              EncSmem<ANY_LMR, ANY_MED>& sm, const Pre& pre = Pre()) {
+  uint8_t* const tin = sm.tin;
+  uint8_t* const tout = sm.tout;
+  uint8_t* const lin = sm.lin;
+  uint8_t* const lout = sm.lout;
+  uint8_t* const sub = sm.sub;
+  uint32_t* const selt = sm.selt;
+  uint8_t* const halo = sm.halo;
+  uint8_t* const uprow = sm.uprow;
 
   const int t = threadIdx.x;
-  const uint32_t strip = blockIdx.x / nsplit, piece = blockIdx.x % nsplit;
   const int img = (int)__ldg(B.strip_owner + strip);
   const ImgDesc& d = B.desc[img];
   const int H = d.H, W = d.W;
@@ -130,6 +220,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
   const bool LMR = ANY_LMR && d.variant == RDHEI_LMR;
   const bool med = ANY_MED && d.med != 0;
   const uint32_t tiles_x = d.tiles_x, ntiles = tiles_x * d.tiles_y;
+  (void)ntiles;                                                  // index checks only
   const uint32_t qty = strip - __ldg(B.strip_prefix + img);       // output tile row
   const uint32_t per = (tiles_x + nsplit - 1) / nsplit;
   const uint32_t tx0 = piece * per, tx1 = min(tx0 + per, tiles_x);
@@ -190,6 +281,7 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
     }
   };
   fetch(tx0);
+  pre();
 
   for (uint32_t tx = tx0; tx < tx1; tx++) {
     const uint32_t P = nP, U = nU;
@@ -345,9 +437,162 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
   }
 }
 
-void launch_topmap(const Batch& B, bool owner, cudaStream_t st) {
+template <bool ANY_LMR, bool ANY_MED>
+__global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint32_t nsplit) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
+  __shared__ EncSmem<ANY_LMR, ANY_MED> sm;
+  enc_rows_body<ANY_LMR, ANY_MED>(B, blockIdx.x / nsplit, nsplit, blockIdx.x % nsplit, sm);
+}
+
+// Hider's half of the fused encode (Sec. III-A-2 / III-B-2) for one 64-row strip of
+// the rotated image that this CTA has just encrypted: its slots start at stream bit
+// strip_base (k_topmap), so the 8192-pixel chunks are walked in raster order with a
+// running offset.  The strip's message words are K2-encrypted (e = m XOR z2, one
+// ChaCha20 block per thread) into shared memory before the gather starts, while its
+// first loads are in flight; a strip whose message range does not fit is encrypted
+// chunk by chunk instead.  Per chunk: the strip's pixels come back from L2 (written
+// moments ago by this CTA), a block scan places each thread's slots and spread_slots
+// writes them.
+constexpr int STRIP_WORDS = 4096;        // staged message words of one strip (131072 slot bits)
+struct EmbedSmem {
+  uint32_t ebuf[STRIP_WORDS + 1];
+  uint32_t warp_tot[HIDE_THREADS / 32];
+  SlotTables tabs;
+  int staged;
+};
+
+// e words [w_lo, w_lo + nw) of image d's message into buf (MSB-first), and a zero word
+// after them; one ChaCha20 block of z2 per thread, nblk <= HIDE_THREADS blocks
+__device__ __forceinline__ void stage_message(const ImgDesc& d, uint64_t w_lo, uint32_t nw, uint32_t* buf) {
+  const int t = threadIdx.x;
+  const uint64_t j0 = w_lo >> 4;
+  const uint32_t nblk = (uint32_t)(((w_lo + nw - 1) >> 4) - j0 + 1);
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(d.payload);
+  if ((uint32_t)t < nblk) {
+    uint32_t o[16];
+    const uint64_t j = j0 + t;
+    chacha20_block<2>(d.k2, (uint32_t)j, d.n2, o, d.one);
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const uint64_t w = 16 * j + i;
+      if (w >= w_lo && w < w_lo + nw) buf[w - w_lo] = bswap32(__ldg(pay + w) ^ o[i]);
+    }
+  }
+  if (t == 0) buf[nw] = 0u;
+}
+
+struct StripRange {
+  uint64_t G0, send;
+};
+__device__ __forceinline__ StripRange strip_range(const Batch& B, uint32_t s, const ImgDesc& d) {
+  const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+  const uint64_t G0 = B.strip_base[s];
+  return {G0, umin64(G0 + B.strip_tot[s], info->embedded)};
+}
+
+// the whole strip's message words, when they fit (called while phase 1's loads fly)
+__device__ __forceinline__ void stage_strip(const Batch& B, uint32_t s, EmbedSmem& sm) {
+  const ImgDesc& d = B.desc[__ldg(B.strip_owner + s)];
+  const StripRange r = strip_range(B, s, d);
+  int staged = 0;
+  if (r.send > r.G0) {
+    const uint64_t W0 = r.G0 >> 5, W1 = (r.send - 1) >> 5;
+    const uint32_t nw = (uint32_t)(W1 - W0 + 1);
+    const uint32_t nblk = (uint32_t)((W1 >> 4) - (W0 >> 4) + 1);
+    if (nw <= (uint32_t)STRIP_WORDS && nblk <= (uint32_t)HIDE_THREADS) {
+      stage_message(d, W0, nw, sm.ebuf);
+      staged = 1;
+    }
+  }
+  if (threadIdx.x == 0) sm.staged = staged;
+}
+
+__device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSmem& sm) {
+  const int t = threadIdx.x;
+  init_slot_tables(sm.tabs);
+  const int img = (int)__ldg(B.strip_owner + s);
+  const ImgDesc& d = B.desc[img];
+  const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+  const uint32_t ty = s - __ldg(B.strip_prefix + img);
+  const uint64_t W = (uint64_t)d.W;
+  const uint64_t p0 = (uint64_t)ty * TILE * W, p1 = (uint64_t)min((int)(ty + 1) * TILE, d.H) * W;
+  const StripRange r = strip_range(B, s, d);
+  __syncthreads();   // tables; the staged flag and message (written before phase 1's first barrier)
+  if (r.G0 >= r.send) return;
+  const bool staged = sm.staged != 0;
+  const uint64_t W0 = r.G0 >> 5;
+  const uint32_t slots = (uint32_t)slots_of(d, info);
+  const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
+  uint64_t Gc = r.G0;
+  ChunkPx cur;
+  load_run(d, d.dst, p0 + (uint64_t)HIDE_PX * t, p1, true, cur);
+  for (uint64_t c0 = p0; c0 < p1 && Gc < r.send; c0 += SCAN_PX) {
+    ChunkPx nxt;                                             // next chunk in flight
+    load_run(d, d.dst, c0 + SCAN_PX + (uint64_t)HIDE_PX * t, p1, true, nxt);
+    const uint32_t zmask = zero_mask(d, cur);
+    uint32_t Tc;
+    const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, sm.warp_tot, Tc);
+    const uint64_t endc = umin64(Gc + Tc, r.send);
+    if (endc > Gc) {
+      const uint64_t w_lo = Gc >> 5;
+      const uint32_t* sbuf = sm.ebuf + (w_lo - W0);
+      if (!staged) {
+        // message words of this chunk's slot range only
+        const uint32_t nw = (uint32_t)(((endc - 1) >> 5) - w_lo + 1);
+        if (RDHEI_IDX_OK(B.err, nw < (uint32_t)SBUF_WORDS)) stage_message(d, w_lo, nw, sm.ebuf);
+        sbuf = sm.ebuf;
+        __syncthreads();
+      }
+      const uint64_t k0 = Gc + my_off;
+      if (zmask && k0 < endc) {
+        spread_slots(cur.px, zmask, slots, fshift, sbuf, 32 * w_lo, k0, endc, sm.tabs, B.err);
+        uint8_t* dst = d.dst + (c0 + (uint64_t)HIDE_PX * t);
+        if (cur.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+          __stcg(reinterpret_cast<uint4*>(dst), make_uint4(cur.px[0], cur.px[1], cur.px[2], cur.px[3]));
+          __stcg(reinterpret_cast<uint4*>(dst) + 1, make_uint4(cur.px[4], cur.px[5], cur.px[6], cur.px[7]));
+        } else {
+#pragma unroll
+          for (int k = 0; k < HIDE_PX; k++)
+            if (k < cur.valid) dst[k] = (uint8_t)(cur.px[k >> 2] >> (8 * (k & 3)));
+        }
+      }
+      if (!staged) __syncthreads();   // the chunk's message words are rewritten by the next chunk
+    }
+    Gc += Tc;
+    cur = nxt;
+  }
+}
+
+// Fused owner + hider (Sec. III-A-1 then III-A-2; III-B-1 then III-B-2): one CTA per
+// 64-row strip of the rotated image gathers, labels, rotates and encrypts its tiles
+// (as k_enc_rows) and then embeds the payload into that strip.
+template <bool ANY_LMR, bool ANY_MED>
+__global__ void __launch_bounds__(256, 4) k_enc_fused(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
+  __shared__ EncSmem<ANY_LMR, ANY_MED> sm;
+  __shared__ EmbedSmem em;
+  const uint32_t s = blockIdx.x;
+  enc_rows_body<ANY_LMR, ANY_MED>(B, s, 1, 0, sm, [&]() { stage_strip(B, s, em); });
+  __syncthreads();   // the strip's encrypted pixels (and LMR map bits) are in global memory
+  embed_strip(B, s, em);
+}
+
+void launch_topmap(const Batch& B, bool owner, bool fused, cudaStream_t st) {
   if (B.n_images == 0) return;
-  launch_pdl(k_topmap, dim3(B.n_images), dim3(256), 0, st, B, owner ? 1 : 0);
+  launch_pdl(k_topmap, dim3(B.n_images), dim3(256), 0, st, B, owner ? 1 : 0, fused ? 1 : 0);
+}
+void launch_enc_fused(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
+  if (B.total_strips == 0) return;
+  const dim3 grid(B.total_strips), block(256);
+  if (any_med) {
+    if (any_lmr) launch_pdl(k_enc_fused<true, true>, grid, block, 0, st, B);
+    else launch_pdl(k_enc_fused<false, true>, grid, block, 0, st, B);
+  } else {
+    if (any_lmr) launch_pdl(k_enc_fused<true, false>, grid, block, 0, st, B);
+    else launch_pdl(k_enc_fused<false, false>, grid, block, 0, st, B);
+  }
 }
 void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
   if (B.total_strips == 0) return;

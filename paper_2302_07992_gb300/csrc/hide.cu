@@ -12,149 +12,9 @@
 // k_scan writes (hider) or gathers (receiver) each chunk's slots at its offset.  The
 // hider's encryption and count pass share one grid (k_z2_count); the receiver's count
 // pass is k_count.  No CTA ever waits for another.
-#include "common.cuh"
-#include "../../include/rdhei.h"
+#include "slots.cuh"
 
 namespace rdhei {
-
-constexpr int HIDE_THREADS = 256;
-constexpr int HIDE_PX = 32;                          // pixels per thread
-constexpr int SCAN_PX = HIDE_THREADS * HIDE_PX;      // 8192 pixels per chunk
-static_assert(SCAN_PX == CHUNK_PX, "chunk size shared with the host layout");
-constexpr int SBUF_WORDS = 7 * SCAN_PX / 32 + 4;     // slots of one chunk, in 32-bit words
-
-// n (1..32) bits of an MSB-first word array starting at bit idx, right-aligned
-__device__ __forceinline__ uint32_t get_bits(const uint32_t* buf, uint32_t idx, uint32_t n) {
-  const uint32_t w = idx >> 5, sh = idx & 31;
-  const uint64_t v = ((uint64_t)buf[w] << 32) | buf[w + 1];
-  return (uint32_t)((v << sh) >> (64 - n));
-}
-// OR n (1..32) right-aligned bits into an MSB-first shared word array at bit idx
-__device__ __forceinline__ void or_bits(uint32_t* buf, uint32_t idx, uint32_t val, uint32_t n) {
-  const uint32_t w = idx >> 5, sh = idx & 31;
-  const uint64_t run = (((uint64_t)val) << (64 - n)) >> sh;
-  const uint32_t hi = (uint32_t)(run >> 32), lo = (uint32_t)run;
-  if (hi) atomicOr(buf + w, hi);
-  if (lo) atomicOr(buf + w + 1, lo);
-}
-
-// My 32 pixels of a chunk (raw words, loads in flight until first use) and the mask
-// of the redundant (label-0) ones: EMR reads the map from the LSB plane, LMR from the
-// packed rotated map.
-struct ChunkPx {
-  uint32_t px[8];
-  uint32_t lbits;   // LMR: packed map bits of my 32 pixels
-  int valid;
-};
-
-__device__ __forceinline__ void issue_chunk(const ImgDesc& d, uint32_t c, int t, bool need_px, ChunkPx& r) {
-  const uint64_t N = (uint64_t)d.H * d.W;
-  const uint64_t p0 = (uint64_t)c * SCAN_PX + (uint64_t)HIDE_PX * t;
-  r.valid = p0 < N ? (int)umin64(HIDE_PX, N - p0) : 0;
-#pragma unroll
-  for (int i = 0; i < 8; i++) r.px[i] = 0;
-  r.lbits = 0xFFFFFFFFu;
-  const bool lmr = d.variant == RDHEI_LMR;
-  if (need_px || !lmr) {
-    const uint8_t* src = d.src + p0;
-    if (r.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(src)), e = __ldcs(reinterpret_cast<const uint4*>(src + 16));
-      r.px[0] = a.x; r.px[1] = a.y; r.px[2] = a.z; r.px[3] = a.w;
-      r.px[4] = e.x; r.px[5] = e.y; r.px[6] = e.z; r.px[7] = e.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < HIDE_PX; k++)
-        if (k < r.valid) r.px[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
-    }
-  }
-  if (lmr && r.valid > 0) r.lbits = stream_bits32(d.map_bits, (N + 31) >> 5, p0);
-}
-
-__device__ __forceinline__ uint32_t zero_mask(const ImgDesc& d, const ChunkPx& r) {
-  uint32_t z;
-  if (d.variant != RDHEI_LMR) {
-    // LSB == 0, pixel 4i+k -> bit 4i+k: the multiply gathers a word's four flags into
-    // bits 28..31 (bit 8k -> 28+k), and the words are shifted in from the last one down
-    z = 0;
-#pragma unroll
-    for (int i = 7; i >= 0; i--) z = __funnelshift_l(((~r.px[i]) & 0x01010101u) * 0x10204080u, z, 4);
-  } else {
-    z = ~r.lbits;
-  }
-  if (r.valid < 32) z &= r.valid <= 0 ? 0u : ((1u << r.valid) - 1u);
-  return z;
-}
-
-__device__ __forceinline__ int slots_of(const ImgDesc& d, const rdhei_info* info) {
-  const int b = d.b > 0 ? d.b : info->b;
-  return d.variant == RDHEI_LMR ? b - 1 : b;
-}
-
-// PRMT selectors for the 4 pixels of a word with label-0 pattern z (bit q = pixel q):
-//   expand:  byte q <- byte rank(q) of the consecutive fields (4 = zero byte) if z_q;
-//   compact: byte j <- byte of the j-th label-0 pixel (4 = zero byte).
-__host__ __device__ __forceinline__ uint32_t sel_expand(uint32_t z) {
-  uint32_t sel = 0, r = 0;
-  for (int q = 0; q < 4; q++) {
-    const uint32_t nib = ((z >> q) & 1u) ? r++ : 4u;
-    sel |= nib << (4 * q);
-  }
-  return sel;
-}
-__host__ __device__ __forceinline__ uint32_t sel_compact(uint32_t z) {
-  uint32_t sel = 0x4444u, j = 0;
-  for (int q = 0; q < 4; q++)
-    if ((z >> q) & 1u) { sel = (sel & ~(0xFu << (4 * j))) | ((uint32_t)q << (4 * j)); j++; }
-  return sel;
-}
-
-// The same with the fields in reversed byte order (first field in byte 3), which is
-// the order the multiply-based field packing produces and consumes:
-//   expand_rev:  byte q <- byte 3 - rank(q) if z_q, else the zero byte;
-//   compact_rev: byte 3 - j <- byte of the j-th label-0 pixel, unused bytes zero.
-__host__ __device__ __forceinline__ uint32_t sel_expand_rev(uint32_t z) {
-  uint32_t sel = 0, r = 0;
-  for (int q = 0; q < 4; q++) {
-    const uint32_t nib = ((z >> q) & 1u) ? 3u - r++ : 4u;
-    sel |= nib << (4 * q);
-  }
-  return sel;
-}
-__host__ __device__ __forceinline__ uint32_t sel_compact_rev(uint32_t z) {
-  uint32_t sel = 0x4444u, j = 0;
-  for (int q = 0; q < 4; q++)
-    if ((z >> q) & 1u) { sel = (sel & ~(0xFu << (4 * (3 - j)))) | ((uint32_t)q << (4 * (3 - j))); j++; }
-  return sel;
-}
-// 0xFF in the bytes of the label-0 pixels of pattern z
-__host__ __device__ __forceinline__ uint32_t zero_bytes(uint32_t z) {
-  return ((z & 1u) ? 0xFFu : 0u) | ((z & 2u) ? 0xFF00u : 0u) | ((z & 4u) ? 0xFF0000u : 0u) |
-         ((z & 8u) ? 0xFF000000u : 0u);
-}
-
-// Block-wide exclusive scan of one value per thread (256 threads); returns the
-// exclusive prefix and the block total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) warp_tot[warp] = inc;
-  __syncthreads();
-  uint32_t base = 0, tot = 0;
-#pragma unroll
-  for (int i = 0; i < HIDE_THREADS / 32; i++) {
-    const uint32_t u = warp_tot[i];
-    base += i < warp ? u : 0u;
-    tot += u;
-  }
-  __syncthreads();
-  total = tot;
-  return base + inc - v;
-}
 
 // Pass 1 of the payload scan: slot count of every chunk, one warp per chunk.  Chunks
 // are independent, so thousands of warps keep their reads in flight at once (no
@@ -276,14 +136,9 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
   constexpr int EW = (SBUF_WORDS + HIDE_THREADS - 1) / HIDE_THREADS;   // message words per thread
   __shared__ uint32_t sbuf[SBUF_WORDS];   // hider: e words (MSB-first); receiver: raw slot stream
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
-  __shared__ uint32_t s_expand[16], s_expand_rev[16], s_compact_rev[16], s_zb[16];
+  __shared__ SlotTables tabs;
   const int t = threadIdx.x;
-  if (t < 16) {
-    s_expand[t] = sel_expand(t);
-    s_expand_rev[t] = sel_expand_rev(t);
-    s_compact_rev[t] = sel_compact_rev(t);
-    s_zb[t] = zero_bytes(t);
-  }
+  init_slot_tables(tabs);
   __syncthreads();
   const uint32_t* cnt = reinterpret_cast<const uint32_t*>(B.chunk_status);
   const uint32_t* off = cnt + B.total_chunks;
@@ -303,7 +158,6 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
     const uint32_t slots = (uint32_t)slots_of(d, info);
     const uint32_t top = d.variant == RDHEI_LMR ? 6u : 7u;
     const uint32_t fshift = top + 1 - slots;
-    const uint32_t fmask = (1u << slots) - 1u;
     const uint32_t c = g - d.chunk_base;
     const uint64_t p0 = (uint64_t)c * SCAN_PX + (uint64_t)HIDE_PX * t;
 
@@ -347,64 +201,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
       }
       if (t == 0) sbuf[nw] = 0u;
       __syncthreads();
-      const uint32_t FREP = (fmask << fshift) * 0x01010101u;
-      const uint32_t my_bits = (uint32_t)__popc(zmask) * slots;
-      if (zmask && G + my_off + my_bits <= d.nbits) {
-        // all my slots lie inside the message.  Per 4-pixel word: the next 32 stream
-        // bits (left-aligned) hold the word's fields f0..f3 (first field most
-        // significant); multiply-adds place f_k at bit fshift of byte 3 - k (the shifts
-        // (3 - k)(8 - s) + fshift are all >= 0), one byte permute moves field r to the
-        // r-th label-0 pixel, and a select writes the slot bits
-        const uint32_t dsh = 8u - slots;
-        const uint32_t m1 = fmask << slots, m2 = fmask << (2 * slots), m3 = fmask << (3 * slots);
-        const uint32_t u0 = 1u << fshift, u1 = u0 << dsh, u2 = u1 << dsh, u3 = u2 << dsh;
-        uint32_t idx = (uint32_t)(G + my_off - 32 * w_lo);          // stream position in sbuf
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
-          const uint32_t w = idx >> 5;
-          if (!RDHEI_IDX_OK(B.err, w + 1 < SBUF_WORDS)) break;
-          const uint32_t E = __funnelshift_l(sbuf[w + 1], sbuf[w], idx & 31);
-          const uint32_t F = E >> (32 - 4 * slots);                 // f0 .. f3, right-aligned
-          const uint32_t cons = (F & fmask) * u0 + (F & m1) * u1 + (F & m2) * u2 + (F & m3) * u3;
-          const uint32_t m = s_zb[zw] & FREP;
-          cur.px[i] = (cur.px[i] & ~m) | __byte_perm(cons, 0, s_expand_rev[zw]);
-          idx += (uint32_t)__popc(zw) * slots;
-        }
-      } else if (zmask && G + my_off < d.nbits) {
-        // the message ends inside my slots.  Per 4-pixel word: read the word's slots at
-        // once, spread the fields to consecutive bytes, then move them to their pixels
-        // with one byte permute; the slots past the message end keep their bits
-        const uint64_t base = 32 * w_lo;
-        const uint32_t s2 = 2 * slots, s3 = 3 * slots;
-        uint64_t k = G + my_off;
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
-          const uint32_t nb = (uint32_t)__popc(zw) * slots;         // <= 28 bits
-          if (nb && k < d.nbits && RDHEI_IDX_OK(B.err, ((k - base) >> 5) + 1 < SBUF_WORDS)) {
-            const uint32_t avail = (uint32_t)umin64(nb, d.nbits - k);
-            const uint32_t E = get_bits(sbuf, (uint32_t)(k - base), avail) << (32 - avail);   // left-aligned
-            const uint32_t rs = 32 - slots;
-            const uint32_t cons = (E >> rs) | (((E << slots) >> rs) << 8) | (((E << s2) >> rs) << 16) |
-                                  (((E << s3) >> rs) << 24);
-            const uint32_t zb = ((zw * 0x00204081u) & 0x01010101u) * 0xFFu;   // label-0 bytes
-            uint32_t m = zb & FREP;
-            if (avail < nb) {
-              // the message ends inside this word: only its first `avail` slot bits
-              uint32_t part = 0, left = avail;
-              for (int j = 0; j < 4; j++) {
-                const uint32_t n = left < slots ? left : slots;
-                part |= (fmask & ~(fmask >> n)) << (8 * j);
-                left -= n;
-              }
-              m &= __byte_perm(part << fshift, 0, s_expand[zw]);
-            }
-            cur.px[i] = (cur.px[i] & ~m) | (__byte_perm(cons << fshift, 0, s_expand[zw]) & m);
-          }
-          k += nb;
-        }
-      }
+      spread_slots(cur.px, zmask, slots, fshift, sbuf, 32 * w_lo, G + my_off, d.nbits, tabs, B.err);
       uint8_t* dst = d.dst + p0;
       if (cur.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
         __stcs(reinterpret_cast<uint4*>(dst), make_uint4(cur.px[0], cur.px[1], cur.px[2], cur.px[3]));
@@ -417,40 +214,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
     } else {
       for (int i = t; i < (int)((Tb >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
       __syncthreads();
-      // gather my slots into the chunk-local stream.  Per 4-pixel word one byte permute
-      // puts the j-th label-0 pixel in byte 3 - j; masked to the field bits, the fields
-      // are packed most-significant first by multiply-adds (byte j moves up by
-      // (4 - j)(8 - s)) and appended to a word that is stored once full: the words
-      // wholly inside my range are plain stores, the two I share with my neighbours are
-      // OR-ed (the range was cleared above)
-      {
-        const uint32_t FREP = fmask * 0x01010101u;
-        const uint32_t dsh = 8u - slots;
-        const uint32_t v3 = 1u << dsh, v2 = v3 << dsh, v1 = v2 << dsh, v0 = v1 << dsh;
-        uint32_t wi = my_off >> 5, c = my_off & 31, word = 0;
-        bool first = true;
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
-          const uint32_t nb = (uint32_t)__popc(zw) * slots;
-          const uint32_t fld = (__byte_perm(cur.px[i], 0, s_compact_rev[zw]) >> fshift) & FREP;
-          const uint32_t P = (fld & 0xFFu) * v0 + (fld & 0xFF00u) * v1 + (fld & 0xFF0000u) * v2 +
-                             (fld & 0xFF000000u) * v3;                 // nb bits, left-aligned
-          word |= P >> c;
-          c += nb;
-          if (c >= 32) {
-            if (RDHEI_IDX_OK(B.err, wi < SBUF_WORDS)) {
-              if (first) atomicOr(sbuf + wi, word);
-              else sbuf[wi] = word;
-            }
-            first = false;
-            c -= 32;
-            word = P << (nb - c);                                     // the bits that spilled over
-            wi++;
-          }
-        }
-        if (c && RDHEI_IDX_OK(B.err, wi < SBUF_WORDS)) atomicOr(sbuf + wi, word);
-      }
+      gather_slots(cur.px, zmask, slots, fshift, my_off, sbuf, tabs, B.err);
       __syncthreads();
       // words of [G, min(G + T, E)), E = bits the receiver asked for and the image holds
       const uint64_t E = info->extracted;
@@ -475,6 +239,107 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
     cur = nxt;
     G = Gn;
     T = Tn;
+  }
+}
+
+// Fused decode, K2 half (Sec. III-A-3 / III-B-3, "receiver has only K2", run inside
+// the both-keys decode): one CTA per 64-row strip of the marked image.  The strip's
+// slots start at the stream bit k_topmap derived from per-tile label counts, so the
+// CTA walks its 8192-pixel chunks in raster order with a running offset -- no count
+// pass, no cross-CTA wait.  The K2 keystream of the strip's message words is computed
+// once, one ChaCha20 block per thread, while the first chunk's loads are in flight (a
+// strip whose range does not fit the buffer computes it chunk by chunk).  Each chunk's
+// slots are gathered into shared memory, XOR-ed with the keystream and stored: words
+// inside the chunk's range whole, words shared with a neighbouring chunk or strip with
+// atomicOr into words that start at zero (cleared by k_topmap at strip ends, here at
+// chunk ends).
+constexpr int Z2_STRIP_WORDS = 16 * HIDE_THREADS;   // 256 keystream blocks
+static_assert(Z2_STRIP_WORDS >= Z2BUF_WORDS, "the strip buffer also holds one chunk's keystream");
+
+// keystream words of blocks [j0, j0 + nblk) into z2 (one block per thread)
+__device__ __forceinline__ void z2_blocks(const ImgDesc& d, uint64_t j0, uint32_t nblk, uint32_t* z2) {
+  const int t = threadIdx.x;
+  if ((uint32_t)t < nblk) {
+    uint32_t o[16];
+    chacha20_block<2>(d.k2, (uint32_t)(j0 + t), d.n2, o, d.one);
+#pragma unroll
+    for (int i = 0; i < 16; i++) z2[16 * t + i] = o[i];
+  }
+}
+
+__global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
+  pdl_wait();      // the previous kernel of the operation has finished
+  pdl_trigger();
+  __shared__ uint32_t sbuf[SBUF_WORDS];
+  __shared__ uint32_t z2buf[Z2_STRIP_WORDS];
+  __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
+  __shared__ SlotTables tabs;
+  const int t = threadIdx.x;
+  init_slot_tables(tabs);
+  const uint32_t s = blockIdx.x;
+  const int img = (int)__ldg(B.strip_owner + s);
+  const ImgDesc& d = B.desc[img];
+  const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
+  const uint32_t ty = s - __ldg(B.strip_prefix + img);
+  const uint64_t W = (uint64_t)d.W;
+  const uint64_t p0 = (uint64_t)ty * TILE * W, p1 = (uint64_t)min((int)(ty + 1) * TILE, d.H) * W;
+  const uint64_t G0 = B.strip_base[s];
+  const uint64_t send = umin64(G0 + B.strip_tot[s], info->extracted);
+  if (G0 >= send) return;                                    // uniform: no slots to read
+  const uint32_t slots = (uint32_t)slots_of(d, info);
+  const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
+  uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
+  const uint64_t out_words = (d.max_bits + 31) >> 5;
+  (void)out_words;                                           // index checks only
+  ChunkPx cur;
+  load_run(d, d.src, p0 + (uint64_t)HIDE_PX * t, p1, false, cur);
+  // the strip's keystream, while the first chunk's loads are in flight
+  const uint64_t J0 = (G0 >> 5) >> 4;
+  const uint32_t nblkS = (uint32_t)((((send - 1) >> 5) >> 4) - J0 + 1);
+  const bool staged = nblkS <= (uint32_t)HIDE_THREADS;
+  if (staged) z2_blocks(d, J0, nblkS, z2buf);
+  __syncthreads();   // tables, keystream
+  uint64_t Gc = G0;
+  for (uint64_t c0 = p0; c0 < p1 && Gc < send; c0 += SCAN_PX) {
+    ChunkPx nxt;                                             // next chunk in flight
+    load_run(d, d.src, c0 + SCAN_PX + (uint64_t)HIDE_PX * t, p1, false, nxt);
+    const uint32_t zmask = zero_mask(d, cur);
+    uint32_t Tc;
+    const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, warp_tot, Tc);
+    const uint64_t endc = umin64(Gc + Tc, send);
+    if (endc > Gc) {
+      for (int i = t; i < (int)((Tc >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
+      const uint64_t wa = Gc >> 5, wb = (endc - 1) >> 5;
+      uint64_t zbase = 16 * J0;                              // word index of z2buf[0]
+      if (!staged) {
+        zbase = 16 * (wa >> 4);
+        z2_blocks(d, wa >> 4, (uint32_t)((wb >> 4) - (wa >> 4) + 1), z2buf);
+      }
+      // a word that starts inside this chunk and ends inside the next one of this strip
+      // is cleared here, before the ORs of both; the word holding the strip's end (shared
+      // with the next strip, or the last one) was cleared by k_topmap
+      if (t == 0 && (endc & 31) && ((endc >> 5) << 5) >= Gc && (endc >> 5) < (send >> 5) &&
+          RDHEI_IDX_OK(B.err, (endc >> 5) < out_words))
+        out[endc >> 5] = 0u;
+      __syncthreads();
+      gather_slots(cur.px, zmask, slots, fshift, my_off, sbuf, tabs, B.err);
+      __syncthreads();
+      for (uint64_t w = wa + t; w <= wb; w += HIDE_THREADS) {
+        const uint64_t b0 = 32 * w;
+        const uint64_t lo = b0 > Gc ? b0 : Gc, hi = b0 + 32 < endc ? b0 + 32 : endc;   // my bits of word w
+        if (!RDHEI_IDX_OK(B.err, w < out_words && ((lo - Gc) >> 5) + 1 < SBUF_WORDS &&
+                                     w - zbase < (uint64_t)Z2_STRIP_WORDS))
+          continue;
+        const uint32_t raw = get_bits(sbuf, (uint32_t)(lo - Gc), (uint32_t)(hi - lo)) << (uint32_t)(b0 + 32 - hi);
+        const uint32_t keep = (0xFFFFFFFFu >> (uint32_t)(lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (uint32_t)(hi - b0));
+        const uint32_t v = bswap32(raw) ^ (z2buf[w - zbase] & bswap32(keep));
+        if (lo == b0 && hi == b0 + 32) out[w] = v;
+        else atomicOr(out + w, v);
+      }
+      __syncthreads();   // sbuf (and an unstaged keystream) are rewritten by the next chunk
+    }
+    Gc += Tc;
+    cur = nxt;
   }
 }
 
@@ -595,6 +460,10 @@ void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st) {
   const uint32_t grid = (B.total_z2_blocks + 127) / 128;
   if (decrypt) launch_pdl(k_z2_xor<true>, dim3(grid), dim3(128), 0, st, B);
   else launch_pdl(k_z2_xor<false>, dim3(grid), dim3(128), 0, st, B);
+}
+void launch_extract_strips(const Batch& B, cudaStream_t st) {
+  if (B.total_strips == 0) return;
+  launch_pdl(k_extract_strips, dim3(B.total_strips), dim3(HIDE_THREADS), 0, st, B);
 }
 void launch_lmr_side(const Batch& B, cudaStream_t st) {
   if (B.total_chunks == 0) return;

@@ -229,8 +229,11 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
       if (lane == 0) { zero_cnt[warp][k] = z & 0xFFFFu; zero_cnt[warp][k + 1] = z >> 16; }
     }
   } else {
-    // K1 receiver: decrypt into the stash, keep the map bit, and record the aux plane
+    // K1 receiver: decrypt into the stash, keep the map bit, and record the aux plane.
+    // Also counts this row's label-0 pixels, the payload slots a K2 receiver reads (EMR:
+    // LSB 0; LMR: map bit 0); the fused decode sums them per strip.
     uint64_t auxbits = 0;
+    uint32_t zrow = 0;
     uint8_t* st = d.stash + base;
     if (d.variant == 0) {
       // the LSBs of s, pixel 4i+k -> aux bit 4i+k: the multiply gathers a word's four
@@ -240,12 +243,14 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
 #pragma unroll
       for (int i = 15; i >= 0; i--) {
         const uint32_t s = sw[i];
+        zrow += (uint32_t)__popc(~px[i] & 0x01010101u);
         px[i] ^= s & 0xFEFEFEFEu;                       // bits 7..1 decrypted, LSB = map l
         const uint32_t x = (s & 0x01010101u) * 0x10204080u;
         if (i >= 8) ahi = push_nibble(ahi, x);
         else alo = push_nibble(alo, x);
       }
       auxbits = ((uint64_t)ahi << 32) | alo;
+      zrow -= (uint32_t)(64 - len);                     // bytes past the row end were loaded as 0
     } else {
       const uint64_t nw = ((uint64_t)H * W + 31) >> 5;
       uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, base) : 0u;
@@ -260,7 +265,11 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
         px[i] = ((px[i] ^ sw[i]) & 0x7F7F7F7Fu) | lbytes;   // bits 6..0 decrypted, bit 7 = map l
       }
       auxbits = eb;
+      const uint64_t valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
+      zrow = (uint32_t)__popcll(~lb & valid);
     }
+    zrow = __reduce_add_sync(0xffffffffu, zrow);
+    if (lane == 0) zero_cnt[warp][0] = zrow;
     if (len < 64) auxbits &= len > 0 ? ((len == 64) ? ~0ull : ((1ull << len) - 1)) : 0ull;
     if (len > 0) {
       if (vec && ((reinterpret_cast<uintptr_t>(st) & 15) == 0)) {
@@ -355,8 +364,11 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
     for (int i = r; i < SUBTREE_BYTES / 4; i += 64) g32[i] = s32[i];
   }
   if (MODE == MODE_ENC && r < 8) {
-    atomicAdd(B.hist_acc + 16 * img + r, zero_cnt[0][r] + zero_cnt[1][r]);
+    const uint32_t zc = zero_cnt[0][r] + zero_cnt[1][r];
+    atomicAdd(B.hist_acc + 16 * img + r, zc);
+    if (B.tile_cnt) B.tile_cnt[8 * (size_t)g + r] = (uint16_t)zc;   // label-0 pixels of this tile for b = r + 1
   }
+  if (MODE == MODE_DEC && r == 0 && B.tile_cnt) B.tile_cnt[8 * (size_t)g] = (uint16_t)(zero_cnt[0][0] + zero_cnt[1][0]);
 }
 
 // The workspace's zero region (error word, tickets, counters, flags), cleared at the

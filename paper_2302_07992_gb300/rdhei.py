@@ -19,6 +19,8 @@ EMR, LMR = 0, 1
 # the related-work variants: MED (LOCO-I) prediction instead of the paper's glide
 EMR_MED, LMR_MED = 2, 3
 OP_LABEL_ENCRYPT, OP_EMBED, OP_EXTRACT, OP_DECRYPT_RECOVER, OP_LMR_SET_SIDE = 0, 1, 2, 3, 4
+# fused calls: owner + hider, and the receiver with both keys
+OP_ENCODE, OP_DECODE = 5, 6
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECAPACITY", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESPACE", 6: "EBOUNDS"}
 RDHEI_OK, RDHEI_EINVAL, RDHEI_ECAPACITY, RDHEI_ECUDA, RDHEI_ETIMEOUT, RDHEI_ESPACE, RDHEI_EBOUNDS = range(7)
 RDHEI_BUILD_CHECKED = 1
@@ -57,7 +59,8 @@ INFO_BYTES = ctypes.sizeof(Info)
 _JobP = ctypes.POINTER(Job)
 _lib.rdhei_workspace_size.argtypes = [_JobP, ctypes.c_int]
 _lib.rdhei_workspace_size.restype = ctypes.c_size_t
-for _n in ("rdhei_label_encrypt", "rdhei_embed", "rdhei_extract", "rdhei_decrypt_recover", "rdhei_lmr_set_side"):
+for _n in ("rdhei_label_encrypt", "rdhei_embed", "rdhei_extract", "rdhei_decrypt_recover", "rdhei_lmr_set_side",
+           "rdhei_encode", "rdhei_decode"):
     getattr(_lib, _n).argtypes = [_JobP, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
     getattr(_lib, _n).restype = ctypes.c_int
 _lib.rdhei_plan_create.argtypes = [_JobP, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
@@ -271,7 +274,8 @@ def run_jobs(op: int, jobs: list[Job], stream=None, check: bool = True) -> int:
     ws = torch.empty(int(need) + 256, dtype=torch.uint8, device="cuda")
     off = (-ws.data_ptr()) % 256
     fn = {OP_LABEL_ENCRYPT: _lib.rdhei_label_encrypt, OP_EMBED: _lib.rdhei_embed, OP_EXTRACT: _lib.rdhei_extract,
-          OP_DECRYPT_RECOVER: _lib.rdhei_decrypt_recover, OP_LMR_SET_SIDE: _lib.rdhei_lmr_set_side}[op]
+          OP_DECRYPT_RECOVER: _lib.rdhei_decrypt_recover, OP_LMR_SET_SIDE: _lib.rdhei_lmr_set_side,
+          OP_ENCODE: _lib.rdhei_encode, OP_DECODE: _lib.rdhei_decode}[op]
     st = _stream(stream)
     _check(fn(arr, len(jobs), ctypes.c_void_p(ws.data_ptr() + off), ws.numel() - off, st), f"op {op}")
     code = ctypes.c_int32(0)
@@ -329,6 +333,36 @@ def decrypt_recover(marked: torch.Tensor, p: Params, b: int, lmr_map: torch.Tens
     j = make_job(p, H, W, src=marked.contiguous(), dst=out, map_bits=lmr_map, eta_bits=lmr_eta, info=info, b=b)
     run_jobs(OP_DECRYPT_RECOVER, [j], stream)
     return out
+
+
+def encode(img: torch.Tensor, p: Params, payload: torch.Tensor, nbits: int, side_bits: torch.Tensor | None = None,
+           side_nbits: int = 0, info: torch.Tensor | None = None, stream=None) -> dict:
+    """rdhei_encode: the owner's label_encrypt and the hider's embed in one call."""
+    H, W = img.shape
+    out = torch.empty_like(img)
+    info = new_info(1) if info is None else info
+    lmr = (p.variant & 1) == LMR
+    mb = bitbuf(H * W)
+    eb = bitbuf(H * W) if lmr else None
+    sb = None if side_bits is None else as_bitbuf(side_bits, side_nbits)
+    pay = as_bitbuf(payload, nbits)
+    j = make_job(p, H, W, src=img.contiguous(), dst=out, map_bits=mb, eta_bits=eb, side_bits=sb,
+                 side_nbits=side_nbits, payload=pay, nbits=nbits, info=info)
+    code = run_jobs(OP_ENCODE, [j], stream)
+    return {"marked": out, "map_bits": mb, "eta_bits": eb, "status": code, "info": info, **read_info(info)[0]}
+
+
+def decode(marked: torch.Tensor, p: Params, b: int, max_bits: int, lmr_map: torch.Tensor | None = None,
+           lmr_eta: torch.Tensor | None = None, info: torch.Tensor | None = None, stream=None) -> dict:
+    """rdhei_decode: the receiver with both keys (extract and decrypt_recover in one call)."""
+    H, W = marked.shape
+    info = new_info(1) if info is None else info
+    out = torch.empty_like(marked)
+    bits = bitbuf(max_bits)
+    j = make_job(p, H, W, src=marked.contiguous(), dst=out, map_bits=lmr_map, eta_bits=lmr_eta, bits_out=bits,
+                 max_bits=max_bits, info=info, b=b)
+    run_jobs(OP_DECODE, [j], stream)
+    return {"bits": bits, "recovered": out, **read_info(info)[0]}
 
 
 def lmr_set_side(enc: torch.Tensor, p: Params, side_bits: torch.Tensor, side_nbits: int, stream=None) -> torch.Tensor:

@@ -23,9 +23,10 @@ def lib():
     return ctypes.CDLL(path)
 
 
-def test_header_declares_the_four_calls():
+def test_header_declares_the_four_calls_and_the_fused_pair():
     names = _declared()
-    for n in ("rdhei_label_encrypt", "rdhei_embed", "rdhei_extract", "rdhei_decrypt_recover"):
+    for n in ("rdhei_label_encrypt", "rdhei_embed", "rdhei_extract", "rdhei_decrypt_recover", "rdhei_encode",
+              "rdhei_decode"):
         assert n in names
 
 
