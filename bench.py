@@ -211,6 +211,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# --------------------------------------------------------- measured ceilings --
+def measure_ceilings(rd, torch, dev, local_rank, reps: int = 5) -> dict:
+    """The integer/logic pipe and the ChaCha20 keystream alone, timed with CUDA events
+    on this GPU (the library's probe kernels; median of `reps` launches after two
+    warm-up launches), with the SM clock sampled meanwhile."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    alu_blocks, alu_iters = sms * 8, 40000            # 8 CTAs of 256 threads per SM
+    ks_blocks, ks_per = sms * 8, 384
+    out = torch.empty(max(alu_blocks, ks_blocks) * rd.PROBE_THREADS, dtype=torch.int32, device=dev)
+    kp = rd.KeystreamProbe(rd.Params(k1=bytes(range(32)), nonce1=bytes(12)), device=dev)
+
+    def timed(launch):
+        for _ in range(2):
+            launch()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.2)
+        alu_ms = timed(lambda: rd.probe_alu(out, alu_blocks, alu_iters, stream))
+        ks_ms = timed(lambda: kp.launch(out, ks_blocks, ks_per, stream))
+    alu_ops = alu_blocks * rd.PROBE_THREADS * alu_iters * rd.PROBE_ALU_OPS_PER_ITER
+    ks_bytes = ks_blocks * rd.PROBE_THREADS * ks_per * 64
+    return {"alu_tops": alu_ops / (alu_ms * 1e-3) / 1e12, "alu_ms": alu_ms,
+            "keystream_gbs": ks_bytes / (ks_ms * 1e-3) / 1e9, "keystream_ms": ks_ms,
+            "clocks": clk.summary(),
+            "how": f"rdhei_probe_alu: {alu_blocks} CTAs x 256 threads x {alu_iters} iterations x 16 LOP3/SHF; "
+                   f"rdhei_probe_keystream: {ks_blocks} CTAs x 256 threads x {ks_per} ChaCha20 blocks "
+                   f"(the path's block function); median of {reps} event-timed launches after 2 warm-ups"}
+
+
 # -------------------------------------------------------------------- GPU arm --
 def run_gpu(args, rank, world, local_rank):
     import torch
@@ -379,6 +419,7 @@ def run_gpu(args, rank, world, local_rank):
     # end to end through the public API with host buffers: H2D inputs, four calls,
     # D2H results, every step
     e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec, wave_cols)
+    ceilings = measure_ceilings(rd, torch, dev, local_rank)
 
     clocks = clk.summary()
     return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "K_breakdown": K2,
@@ -388,7 +429,7 @@ def run_gpu(args, rank, world, local_rank):
             "kernels_per_step": sum(1 + (s_ == 0) + (nm == "extract_count")
                                     for _, _, s_, nm in stage_list),
             "verify": verify, "e2e": e2e, "clocks": clocks, "stage_list": [x[3] for x in stage_list],
-            "caps": caps, "variants": variants, "tuning": tuning}
+            "caps": caps, "variants": variants, "tuning": tuning, "ceilings": ceilings}
 
 
 def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec_ref, wave_cols=None):
@@ -575,22 +616,28 @@ def run_c3(args):
 
 
 # ------------------------------------------------------------------ serving --
-def run_c5(args):
-    """Poisson stream of mixed encode / decode requests (image sides log-uniform in
+def serving_runs(args, plan, pool_n=None, window_ms=None):
+    """Poisson streams of mixed encode / decode requests (image sides log-uniform in
     256..4096) through the continuous-batching server under a 40 GB device-memory
-    budget; p50 / p99 latency (arrival -> results in host memory) and sustained
-    Mpixel/s, at the configured rate and at twice it."""
+    budget.  Encodes of LMR images keep their maps on the device; decode requests of
+    pre-encoded images name that state instead of carrying host maps.  plan: a list of
+    (rate multiplier, seconds, timed); an untimed run first fills the device
+    allocator's cache and the pinned result pool.  Returns per timed run: p50 / p99
+    latency (arrival -> results in host memory), offered and sustained Gpx/s, requests
+    per batch."""
     import torch
     from paper_2302_07992_gb300 import rdhei as rd
     from paper_2302_07992_gb300 import serve as sv
     rng = np.random.default_rng(5)
-    n_pool = args.c5_pool
+    n_pool = pool_n or args.c5_pool
+    window = args.c5_window_ms if window_ms is None else window_ms
     sides = np.exp(rng.uniform(np.log(256), np.log(4096), size=(n_pool, 2))).astype(int)
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
         pool_imgs = pool.map(_gen_shape, [(10_000 + k, int(h), int(w)) for k, (h, w) in enumerate(sides)], chunksize=2)
     torch.cuda.set_device(0)
-    # pre-encoded inputs for decode requests: marked images + maps, from one served pass
+    state = sv.DeviceState(cap_bytes=4e9)
+    # pre-encoded inputs for decode requests: marked images, maps kept on the device
     base = []
     for k, img in enumerate(pool_imgs):
         kk = synth.keys(20_000 + k)
@@ -599,13 +646,11 @@ def run_c5(args):
         nbits = img.size // 2
         base.append(sv.Request(rid=k, kind="encode", params=p, image=torch.from_numpy(img).pin_memory(),
                                payload=torch.from_numpy(synth.payload_bits(20_000 + k, nbits)).pin_memory(),
-                               nbits=nbits))
-    pre = {r.rid: r for r in sv.Server().run(base, realtime=False)}
+                               nbits=nbits, keep_state=True))
+    pre = {r.rid: r for r in sv.Server(state=state).run(base, realtime=False)}
     results = {}
-    pinned = sv.PinnedPool()                   # pinned result buffers, recycled across both runs
-    # an untimed second at the configured rate first: the device allocator's cache and
-    # the pinned result pool fill up with the request sizes of this mix
-    for mult, seconds, timed in ((1.0, 1.0, False), (1.0, args.c5_seconds, True), (2.0, args.c5_seconds, True)):
+    pinned = sv.PinnedPool()                   # pinned result buffers, recycled across the runs
+    for mult, seconds, timed in plan:
         rate = args.c5_rate * mult
         n = int(rate * seconds)
         t = np.cumsum(rng.exponential(1.0 / rate, size=n))
@@ -614,34 +659,54 @@ def run_c5(args):
             k = int(rng.integers(n_pool))
             b = base[k]
             if rng.random() < 0.5:
+                # served encodes of LMR images keep no state: nothing decodes them later here
                 reqs.append(sv.Request(rid=i, kind="encode", params=b.params, image=b.image, payload=b.payload,
                                        nbits=b.nbits, arrival=float(t[i])))
             else:
                 pr = pre[k].result
                 reqs.append(sv.Request(rid=i, kind="decode", params=b.params, image=pr["marked"],
-                                       nbits=pr["info"]["embedded"], b=pr["info"]["b"], lmr_map=pr.get("map_bits"),
-                                       lmr_eta=pr.get("eta_bits"), arrival=float(t[i])))
-        server = sv.Server(budget_bytes=40e9, pool=pinned)
+                                       nbits=pr["info"]["embedded"], b=pr["info"]["b"], state=pr.get("state", 0),
+                                       arrival=float(t[i])))
+        server = sv.Server(budget_bytes=40e9, pool=pinned, state=state, admit_window_ms=window)
         done = server.run(reqs, realtime=True, consume=server.release)   # results are consumed on arrival
         if not timed:
             continue
         st = sv.latency_stats(done)
+        st["status"] = {k: sum(r.status == k for r in done) for k in sv.STATUSES}
         st["batches"] = len(server.batches)
         st["requests_per_batch"] = len(done) / max(1, len(server.batches))
         launches = sorted(b["launch_ms"] for b in server.batches)
         st["max_batch_ms"] = max((b["done_ms"] - b["launch_ms"] for b in server.batches), default=0.0)
         st["max_launch_gap_ms"] = max((b - a for a, b in zip(launches, launches[1:])), default=0.0)
         st["offered_req_s"] = rate
-        st["offered_mpx_s"] = sum(r.pixels for r in reqs) / args.c5_seconds / 1e6
+        st["offered_gpx_s"] = sum(r.pixels for r in reqs) / seconds / 1e9
+        st["sustained_gpx_s"] = (st["sustained_mpx"] or 0.0) / 1e3
+        st["admit_window_ms"] = window
+        st["device_state_bytes"] = state.bytes
         results[f"x{mult:g}"] = st
-    first = results["x1"]
+    return results, n_pool
+
+
+def serving_summary(st: dict, seconds: float, rate: float, n_pool: int, window: float) -> dict:
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "offered_gpx_s": st["offered_gpx_s"], "sustained_gpx_s": st["sustained_gpx_s"],
+            "mean_batch": st["requests_per_batch"], "requests": st["requests"], "status": st["status"],
+            "max_batch_ms": st["max_batch_ms"],
+            "workload": f"Poisson {rate:g} req/s for {seconds:g} s after an untimed 1 s, 50/50 encode/decode, "
+                        f"sides log-uniform 256..4096 ({n_pool} distinct images), 40 GB budget, admission window "
+                        f"{window:g} ms, LMR maps of decoded images device-resident"}
+
+
+def run_c5(args):
+    """Serving latency at the configured rate and at twice it (see serving_runs)."""
+    res, n_pool = serving_runs(args, [(1.0, 1.0, False), (1.0, args.c5_seconds, True), (2.0, args.c5_seconds, True)])
+    first = res["x1"]
     return {"metric": "p50/p99 request latency (arrival -> results on host)", "value": first["p99_ms"],
             "unit": "ms (p99)", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": None,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"Poisson {args.c5_rate:g} req/s for {args.c5_seconds:g} s (after an untimed 1 s "
-                                   f"at the same rate), 50/50 encode/decode, sides log-uniform 256..4096 "
-                                   f"({n_pool} distinct images), 40 GB budget"},
-            "serving": results}
+            "config": {"workload": serving_summary(first, args.c5_seconds, args.c5_rate, n_pool,
+                                                   args.c5_window_ms)["workload"]},
+            "serving": res}
 
 
 # ------------------------------------------------------- decode-only stress --
@@ -739,6 +804,7 @@ def run_c4(args):
 
 # ---------------------------------------------------------- security stats --
 FP32_LANES_PER_SM = 128
+SMS = 152
 SSIM_FLOP_PER_WINDOW = 176.0   # 4 local moments (mu_a, mu_b, E[a^2 + b^2], E[ab]) x 11 taps x 2 passes x 2
 
 
@@ -900,13 +966,13 @@ def run_lmr_blocks(args):
 
 
 # ----------------------------------------------------------------- roofline --
-ALU_LANES_PER_SM = 64          # integer/logic pipe lanes per SM (4 sub-partitions x 16)
-SMS = 152
 ALU_OPS_PER_KS_BYTE = 10.0     # ChaCha20: (4 XOR + 4 rotate) per quarter-round, 80 QR / 64 B
 
 
 def roofline(res, peaks, args):
-    """Roofline of the dominant kernel (largest share of the timed region)."""
+    """Roofline of the dominant kernel (largest share of the timed region), against the
+    peaks measured in this run (HBM: MEASURED_PEAKS.json's copy bandwidth; integer
+    pipe and ChaCha20 keystream: the library's probes, timed live)."""
     K = res["K_breakdown"]
     tot = {k: sum(v) for k, v in res["per_stage"].items()}
     dom = res["dominant"]
@@ -937,37 +1003,57 @@ def roofline(res, peaks, args):
         # MED: the gather pass only stages the de-rotated pixels; the wavefront writes I'
         hbm_bytes["dec_gather_recover"] = 0.0
         hbm_bytes["med_wavefront"] = 1.0 * px
+    # keystream bytes each kernel computes (K1: one byte per pixel; K2: the message)
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
                 "z2_encrypt_count": der / 8 * px, "z2_decrypt": der / 8 * px,
                 "enc_gather_embed": der / 8 * px, "extract_strips": der / 8 * px}
-    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * ALU_LANES_PER_SM * clock_mhz * 1e6           # ALU-pipe ops/s
+    ceil = res["ceilings"]
+    alu_peak = ceil["alu_tops"] * 1e12                            # measured ALU-pipe ops/s
+    ks_peak = ceil["keystream_gbs"] * 1e9                         # measured keystream bytes/s
     hbm_peak = peaks.get("hbm_gbs", 6777.0)
     out_all = {}
     for name, t in tot.items():
         a_ms = avg_ms if name == dom else t / K       # the dominant kernel: timed-region events
         hb = hbm_bytes.get(name, 0.0) / (a_ms / 1e3) / 1e9
-        alu = ks_bytes.get(name, 0.0) * ALU_OPS_PER_KS_BYTE / (a_ms / 1e3)
+        ks = ks_bytes.get(name, 0.0) / (a_ms / 1e3)
         out_all[name] = {"ms": a_ms, "share": t / sum(tot.values()), "hbm_gbs": hb, "hbm_frac": hb / hbm_peak,
-                         "alu_tops": alu / 1e12, "alu_frac": alu / alu_peak}
+                         "alu_tops": ks * ALU_OPS_PER_KS_BYTE / 1e12, "alu_frac": ks * ALU_OPS_PER_KS_BYTE / alu_peak,
+                         "keystream_frac": ks / ks_peak}
     d = out_all[dom]
     if d["alu_frac"] >= d["hbm_frac"]:
         roof = {"bound": "alu", "kernel": dom, "achieved": d["alu_tops"], "peak": alu_peak / 1e12,
                 "unit": "Tops/s (integer/logic pipe)", "frac": d["alu_frac"],
-                "peak_source": f"derived: {SMS} SMs x {ALU_LANES_PER_SM} lanes x {clock_mhz:.0f} MHz"}
+                "achieved_basis": f"{ALU_OPS_PER_KS_BYTE:.0f} ALU-pipe ops per ChaCha20 keystream byte the kernel "
+                                  "computes",
+                "peak_source": "measured in this run: rdhei_probe_alu (of measured)"}
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": d["hbm_frac"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+                "frac": d["hbm_frac"], "achieved_basis": "algorithmic bytes per launch / launch time",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof["traffic"] = measured_traffic(dom, px)
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["algorithmic_bytes"] = hbm_bytes.get(dom, 0.0)
     roof["avg_launch_ms"] = avg_ms
+    roof["hbm_frac"] = d["hbm_frac"]
+    roof["alu_peak_measured"] = ceil["alu_tops"]
+    roof["keystream_ceiling_gbs"] = ceil["keystream_gbs"]
+    # the whole step against the keystream ceiling: every keystream byte of the step
+    # (K1 for the owner and the receiver, K2 for the hider and the receiver) at the
+    # probe's rate is the least time any ChaCha20-keyed implementation needs
+    step_ms = res["total_ms"] / res["K"]
+    step_ks = (2.0 + 2 * der / 8) * px
+    roof["step_keystream_floor_ms"] = step_ks / ks_peak * 1e3
+    roof["step_keystream_frac"] = (step_ks / ks_peak * 1e3) / step_ms
+    roof["step_hbm_floor_ms"] = (4.0 + 2 * der / 8) * px / (hbm_peak * 1e9) * 1e3
+    roof["step_hbm_frac"] = roof["step_hbm_floor_ms"] / step_ms
+    roof["ceilings_how"] = ceil["how"]
+    roof["ceilings_clocks"] = ceil["clocks"]
     return roof, out_all
 
 
 # the timed kernels and their launchers (host-only ABI code in api.cu does not change
 # what the kernels move)
-HOT_PATH_SOURCES = ("common.cuh", "decode.cu", "encode.cu", "hide.cu", "pass1.cu", "permute.cuh")
+HOT_PATH_SOURCES = ("common.cuh", "decode.cu", "encode.cu", "hide.cu", "pass1.cu", "permute.cuh", "slots.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -1086,6 +1172,10 @@ def main():
     ap.add_argument("--c5-rate", type=float, default=2000.0)
     ap.add_argument("--c5-seconds", type=float, default=5.0)
     ap.add_argument("--c5-pool", type=int, default=64)
+    ap.add_argument("--c5-window-ms", type=float, default=0.5,
+                    help="serving: while a batch is on the device, hold arrivals up to this long to batch them")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="the default run's serving leg (Poisson 2000 req/s after an untimed second); 0 skips it")
     ap.add_argument("--c3-small", type=int, default=256)
     ap.add_argument("--c3-big", type=int, default=4)
     ap.add_argument("--c4-images", type=int, default=64)
@@ -1157,6 +1247,11 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_gpu(args, rank, world, local_rank)
+    serving = None
+    if world == 1 and args.serve_seconds > 0:
+        # bounded serving leg: request latency of the continuous-batching server
+        sres, n_pool = serving_runs(args, [(1.0, 1.0, False), (1.0, args.serve_seconds, True)], pool_n=48)
+        serving = serving_summary(sres["x1"], args.serve_seconds, args.c5_rate, n_pool, args.c5_window_ms)
     peaks = load_peaks()
     roof, kernels = roofline(res, peaks, args)
     K = res["K"]
@@ -1174,6 +1269,8 @@ def main():
                             "events only around the dominant kernel"}
     if res.get("tuning"):
         line["tuning"] = res["tuning"]
+    if serving is not None:
+        line["serving"] = serving
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -366,6 +366,23 @@ size_t rdhei_side_unpack_job_size(void);
 #define RDHEI_NOALLOC_MAX_PIXELS (1u << 24)
 int rdhei_extract_noalloc(const rdhei_job *job, void *stream);
 
+/* Measurement probes (the paper has no counterpart: they measure this GPU's ceilings
+ * for the roofline of the path's kernels, which are bound by integer work).
+ * rdhei_probe_alu: `blocks` CTAs of 256 threads, each thread running `iters` iterations
+ *   of 8 independent chains of one XOR (LOP3) and one rotation (SHF): 16 integer/logic-
+ *   pipe operations per thread and iteration.  out: device, blocks * 256 words.
+ * rdhei_probe_keystream: `blocks` CTAs of 256 threads, each thread computing
+ *   `per_thread` ChaCha20 blocks of (key_job->k1, key_job->nonce1) with the block
+ *   function of the path's kernels and XOR-folding them into one word: 64 keystream
+ *   bytes per block.  out: device, blocks * 256 words; ws: device, 16-byte aligned, at
+ *   least rdhei_probe_workspace_size() bytes (the call waits for its small upload).
+ * Both are asynchronous on `stream` (time them with events); RDHEI_EINVAL for bad
+ * arguments, RDHEI_ECUDA for a failed launch. */
+int rdhei_probe_alu(uint32_t *out, int blocks, int iters, void *stream);
+int rdhei_probe_keystream(uint32_t *out, int blocks, int per_thread, const rdhei_job *key_job, void *ws,
+                          void *stream);
+size_t rdhei_probe_workspace_size(void);
+
 /* Failure-detection self-test of the bounded device-side wait that the MED
  * wavefront's tiles use on their neighbours' done flags: one warp waits until the
  * device word *flag is non-zero or limit_ns nanoseconds of %globaltimer have passed

@@ -387,6 +387,38 @@ def extract_noalloc_job(job: Job, stream=None) -> int:
     return int(_lib.rdhei_extract_noalloc(ctypes.byref(job), _stream(stream)))
 
 
+# ------------------------------------------------------------- measurement probes --
+_lib.rdhei_probe_alu.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+_lib.rdhei_probe_alu.restype = ctypes.c_int
+_lib.rdhei_probe_keystream.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _JobP, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+_lib.rdhei_probe_keystream.restype = ctypes.c_int
+_lib.rdhei_probe_workspace_size.restype = ctypes.c_size_t
+PROBE_THREADS, PROBE_ALU_OPS_PER_ITER = 256, 16
+
+
+def probe_alu(out: torch.Tensor, blocks: int, iters: int, stream=None):
+    """Launch the integer/logic-pipe probe: blocks * 256 threads * iters * 16 ALU ops."""
+    assert out.is_cuda and out.numel() * out.element_size() >= 4 * blocks * PROBE_THREADS
+    _check(_lib.rdhei_probe_alu(ctypes.c_void_p(out.data_ptr()), int(blocks), int(iters), _stream(stream)),
+           "rdhei_probe_alu")
+
+
+class KeystreamProbe:
+    """The ChaCha20 keystream probe: blocks * 256 threads * per_thread blocks of 64 bytes."""
+
+    def __init__(self, p: Params, device="cuda"):
+        self.job = make_job(p, 1, 1)
+        self.ws = torch.empty(int(_lib.rdhei_probe_workspace_size()) + 64, dtype=torch.uint8, device=device)
+        self.ws_ptr = self.ws.data_ptr() + ((-self.ws.data_ptr()) % 16)
+
+    def launch(self, out: torch.Tensor, blocks: int, per_thread: int, stream=None):
+        assert out.is_cuda and out.numel() * out.element_size() >= 4 * blocks * PROBE_THREADS
+        _check(_lib.rdhei_probe_keystream(ctypes.c_void_p(out.data_ptr()), int(blocks), int(per_thread),
+                                          ctypes.byref(self.job), ctypes.c_void_p(self.ws_ptr), _stream(stream)),
+               "rdhei_probe_keystream")
+
+
 # ------------------------------------------------------ security statistics --
 STATS_SSIM = 1
 

@@ -48,6 +48,8 @@ class Request:
     b: int = 0                     # decode: the public b
     lmr_map: Any = None            # LMR decode: packed rotated map
     lmr_eta: Any = None
+    state: int = 0                 # decode: handle of device-resident maps kept by an earlier encode
+    keep_state: bool = False       # encode: keep the LMR maps on the device, return a handle
     arrival: float = 0.0           # seconds on the scheduler clock
     done: float = -1.0
     status: str = ""
@@ -83,9 +85,12 @@ LAT_EDGES_MS = [0.05 * 2.0 ** k for k in range(20)]
 class Scheduler:
     def __init__(self, executor, budget_bytes: float = 40e9, max_batch: int = 64,
                  max_batch_pixels: int = 1 << 27, max_queue: int | None = None,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, admit_window_ms: float = 0.0):
         self.ex = executor
         self.budget = float(budget_bytes)
+        # while a batch is on the device, hold new requests for up to this long so that
+        # they leave together (an idle device takes the first request at once)
+        self.admit_window = admit_window_ms * 1e-3
         self.max_batch = max_batch
         self.max_batch_pixels = max_batch_pixels
         self.max_queue = max_queue
@@ -176,6 +181,9 @@ class Scheduler:
             self._finish(self.queue.popleft(), "cancelled", self.now())
         if not self.queue or len(self.inflight) >= self.ex.slots:
             return []
+        if (self.admit_window > 0 and self.inflight and self.now() - self.queue[0].arrival < self.admit_window
+                and len(self.queue) < self.max_batch):
+            return []
         kind = self.queue[0].kind
         batch, px = [], 0
         while self.queue and len(batch) < self.max_batch:
@@ -186,7 +194,8 @@ class Scheduler:
             if r.kind != kind or px + r.pixels > self.max_batch_pixels and batch:
                 break
             need = r.device_bytes()
-            if self.in_use + need > self.budget and (batch or self.inflight):
+            held = getattr(self.ex, "state_bytes", lambda: 0)()   # device-resident state of earlier requests
+            if self.in_use + held + need > self.budget and (batch or self.inflight):
                 break
             self.queue.popleft()
             self.in_use += need
@@ -256,7 +265,7 @@ class Scheduler:
                 # idle until the next arrival (or a completion)
                 time.sleep(max(0.0, min(pending[0].arrival - self.now(), 2e-4)))
             elif self.queue and self.inflight:
-                time.sleep(2e-5)                  # the budget is held by running batches
+                time.sleep(2e-5)                  # the budget is held by running batches, or the window is open
 
     # ---------------------------------------------------------------- metrics --
     def metrics(self) -> dict:

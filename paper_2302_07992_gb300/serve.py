@@ -5,6 +5,12 @@
   decode request: a marked image (+ LMR maps) -> rdhei_extract + rdhei_decrypt_recover
                   -> message bits and recovered image.
 
+Device-resident state: an encode request with keep_state leaves its rotated LMR maps
+(map l and first-MSB map eta, 2 bits a pixel) in device memory and returns a handle; a
+decode request that names the handle reads them there, so they never cross the host
+link.  The store (DeviceState) is charged to the admission budget and evicts the
+least recently used entries beyond its own cap.
+
 Admission, batching, cancellation, failure handling and metrics are the device-free
 scheduler of ``sched``; this module supplies its CUDA executor.  Each admitted group
 of same-kind requests becomes one batch: one plan per operation over all its images,
@@ -19,7 +25,7 @@ ranges.
 from __future__ import annotations
 
 import math
-from collections import deque
+from collections import OrderedDict, deque
 
 import torch
 
@@ -51,6 +57,38 @@ class PinnedPool:
         self.free.setdefault(base.numel(), []).append(base)
 
 
+class DeviceState:
+    """Per-image LMR maps kept in device memory between an encode and later decodes of
+    the same image, under a byte cap (least recently used entries are evicted)."""
+
+    def __init__(self, cap_bytes: float = 4e9):
+        self.cap = float(cap_bytes)
+        self.items: OrderedDict[int, torch.Tensor] = OrderedDict()
+        self.bytes = 0
+        self._next = 1
+
+    def put(self, buf: torch.Tensor) -> int:
+        h = self._next
+        self._next += 1
+        self.items[h] = buf
+        self.bytes += buf.numel()
+        while self.bytes > self.cap and len(self.items) > 1:
+            _, old = self.items.popitem(last=False)
+            self.bytes -= old.numel()
+        return h
+
+    def get(self, handle: int) -> torch.Tensor | None:
+        buf = self.items.get(handle)
+        if buf is not None:
+            self.items.move_to_end(handle)
+        return buf
+
+    def drop(self, handle: int):
+        buf = self.items.pop(handle, None)
+        if buf is not None:
+            self.bytes -= buf.numel()
+
+
 class _Batch:
     def __init__(self, reqs, stream):
         self.reqs = reqs
@@ -65,12 +103,17 @@ class CudaExecutor:
     """Runs a scheduler batch on the GPU: one stream per batch in flight, one plan per
     operation, pinned result buffers from a PinnedPool."""
 
-    def __init__(self, streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None):
+    def __init__(self, streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None,
+                 state: "DeviceState | None" = None):
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self.free_streams = deque(self.streams)
         self.slots = streams
         self.pool = pool if pool is not None else PinnedPool()
+        self.state = state if state is not None else DeviceState()
+
+    def state_bytes(self) -> int:
+        return self.state.bytes
 
     def launch(self, reqs: list[Request]) -> _Batch:
         st = self.free_streams.popleft()
@@ -123,10 +166,14 @@ class CudaExecutor:
             pl.copy_status(h[i:i + 1], st)
         return h
 
-    def discard(self, result: dict):
+    def discard(self, result: dict, drop_state: bool = True):
+        """Give back a result's pinned buffers; unless drop_state is False, also its
+        device-resident maps (a result nobody will read)."""
         for v in result.values():
             if isinstance(v, torch.Tensor):          # result tensors all come from the pool
                 self.pool.give(v)
+        if drop_state and result.get("state"):
+            self.state.drop(result["state"])
 
     def release(self, bt: _Batch):
         bt.keep.clear()
@@ -157,10 +204,19 @@ class CudaExecutor:
         imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
         enc = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
         marked = [v.view(*r.image.shape) for v, r in zip(views[2 * n:], reqs)]
-        bit_arena, bviews = self._arena([self._words(p) if l else None for p, l in zip(px, lmr)] * 2 +
-                                        [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
+        keep = [l and r.keep_state for l, r in zip(lmr, reqs)]
+        bit_arena, bviews = self._arena([self._words(p) if l and not k else None for p, l, k in zip(px, lmr, keep)]
+                                        * 2 + [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
         maps, etas, pays = bviews[:n], bviews[n:2 * n], bviews[2 * n:3 * n]
         info = bviews[-1].view(n, rd.INFO_BYTES)
+        # maps that stay on the device get an allocation of their own (the store holds it)
+        kept = {}
+        for i, r in enumerate(reqs):
+            if keep[i]:
+                w = self._words(px[i])
+                buf = torch.empty(2 * w, dtype=torch.uint8, device=dev)
+                maps[i], etas[i] = buf[:w], buf[w:]
+                kept[i] = buf
         j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=enc[i], map_bits=maps[i], eta_bits=etas[i],
                           info=info[i]) for i, r in enumerate(reqs)]
         j2 = [rd.make_job(r.params, *r.image.shape, src=enc[i], dst=marked[i], map_bits=maps[i], payload=pays[i],
@@ -176,7 +232,9 @@ class CudaExecutor:
             h = self.pool.take(tuple(r.image.shape))
             h.copy_(marked[i], non_blocking=True)
             o = {"marked": h}
-            if lmr[i]:
+            if i in kept:
+                o["state"] = self.state.put(kept[i])
+            elif lmr[i]:
                 hm = self.pool.take(tuple(maps[i].shape))
                 he = self.pool.take(tuple(etas[i].shape))
                 hm.copy_(maps[i], non_blocking=True)
@@ -193,12 +251,24 @@ class CudaExecutor:
     def _launch_decode(self, bt, reqs, st, dev):
         n = len(reqs)
         px = [r.pixels for r in reqs]
-        img_arena, views = self._arena(px * 2 + [r.lmr_map.numel() if r.lmr_map is not None else None for r in reqs]
-                                       + [r.lmr_eta.numel() if r.lmr_eta is not None else None for r in reqs],
-                                       False, dev)
+        # device-resident maps of an earlier encode, else the request's host maps
+        held = [self.state.get(r.state) if r.state else None for r in reqs]
+        for r, h in zip(reqs, held):
+            if r.state and h is None and r.lmr_map is None:
+                raise KeyError(f"device state {r.state} is gone and the request carries no maps")
+        img_arena, views = self._arena(px * 2 + [r.lmr_map.numel() if r.lmr_map is not None and h is None else None
+                                                 for r, h in zip(reqs, held)]
+                                       + [r.lmr_eta.numel() if r.lmr_eta is not None and h is None else None
+                                          for r, h in zip(reqs, held)], False, dev)
         imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
         rec = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
         maps, etas = views[2 * n:3 * n], views[3 * n:]
+        for i, h in enumerate(held):
+            if h is not None:
+                w = h.numel() // 2
+                maps[i], etas[i] = h[:w], h[w:]
+                h.record_stream(st)                 # allocated on the encode's stream, read on this one
+                bt.keep.append(h)                   # alive until the batch completes, even if evicted
         bit_arena, bviews = self._arena([self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
         bits, info = bviews[:n], bviews[-1].view(n, rd.INFO_BYTES)
         j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], map_bits=maps[i], bits_out=bits[i], max_bits=r.nbits,
@@ -208,7 +278,7 @@ class CudaExecutor:
         p1, p2 = rd.Plan(j1, st), rd.Plan(j2, st)
         for i, r in enumerate(reqs):
             imgs[i].copy_(r.image, non_blocking=True)
-            if maps[i] is not None:
+            if maps[i] is not None and held[i] is None:
                 maps[i].copy_(r.lmr_map.reshape(-1), non_blocking=True)
                 etas[i].copy_(r.lmr_eta.reshape(-1), non_blocking=True)
         p1.run(rd.OP_EXTRACT, st)
@@ -233,13 +303,18 @@ class Server(Scheduler):
 
     def __init__(self, budget_bytes: float = 40e9, max_batch: int = 64, max_batch_pixels: int = 1 << 27,
                  streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None,
-                 max_queue: int | None = None):
-        ex = CudaExecutor(streams, device, pool)
-        super().__init__(ex, budget_bytes, max_batch, max_batch_pixels, max_queue)
+                 max_queue: int | None = None, state: "DeviceState | None" = None, admit_window_ms: float = 0.0):
+        ex = CudaExecutor(streams, device, pool, state)
+        super().__init__(ex, budget_bytes, max_batch, max_batch_pixels, max_queue, admit_window_ms=admit_window_ms)
         self.pool = ex.pool
+        self.state = ex.state
 
     def release(self, r: Request):
         """Give a completed request's pinned result buffers back for reuse; the result
-        tensors must not be read afterwards."""
-        self.ex.discard(r.result)
-        r.result = {"info": r.result.get("info")}
+        tensors must not be read afterwards.  Device-resident maps stay (their handle
+        is kept in the result) until drop_state() or eviction."""
+        self.ex.discard(r.result, drop_state=False)
+        r.result = {"info": r.result.get("info"), "state": r.result.get("state", 0)}
+
+    def drop_state(self, handle: int):
+        self.state.drop(handle)

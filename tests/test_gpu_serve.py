@@ -39,7 +39,8 @@ def _encode_requests(rd, sv, n, seed0):
 
 def _clone(sv, r):
     return sv.Request(rid=r.rid, kind=r.kind, params=r.params, image=r.image, payload=r.payload, nbits=r.nbits, b=r.b,
-                      lmr_map=r.lmr_map, lmr_eta=r.lmr_eta, arrival=r.arrival)
+                      lmr_map=r.lmr_map, lmr_eta=r.lmr_eta, arrival=r.arrival, state=r.state,
+                      keep_state=r.keep_state)
 
 
 def _same(a, b):
@@ -108,3 +109,52 @@ def test_budget_admission(mods):
     srv = sv.Server(budget_bytes=one * 1.5, max_batch=8, streams=4)   # at most one request in flight
     done = srv.run(reqs, realtime=False)
     assert len(done) == 6 and srv.in_use == pytest.approx(0.0)
+
+
+def test_device_resident_maps_and_admission_window(mods):
+    """Encodes that keep their LMR maps on the device hand back a handle instead of host
+    maps; decodes that name the handle read the maps in place and give the same bytes
+    as decodes fed the maps from the host, with the server's admission window on."""
+    rd, sv = mods
+    enc = _encode_requests(rd, sv, 10, 21)
+    srv = sv.Server(max_batch=8, streams=2, admit_window_ms=2.0)
+    kept = []
+    for r in enc:
+        c = _clone(sv, r)
+        c.keep_state = True
+        c.arrival = 0.0                             # all at once: they cannot all go one by one
+        kept.append(c)
+    done = {r.rid: r for r in srv.run(kept, realtime=True)}
+    assert max(b["requests"] for b in srv.batches) > 1, "no two requests left together"
+    ref = {r.rid: sv.Server(max_batch=1, streams=1).run([_clone(sv, r)], realtime=False)[0] for r in enc}
+    dec_state, dec_host = [], []
+    for r in enc:
+        got, alone = done[r.rid].result, ref[r.rid].result
+        assert torch.equal(got["marked"], alone["marked"])
+        inf = got["info"]
+        lmr = r.params.variant == rd.LMR
+        if lmr:
+            assert got.get("state") and "map_bits" not in got
+            assert srv.state.get(got["state"]) is not None
+        else:
+            assert not got.get("state")
+        dec_state.append(sv.Request(rid=100 + r.rid, kind="decode", params=r.params, image=got["marked"],
+                                    nbits=inf["embedded"], b=inf["b"], state=got.get("state", 0)))
+        dec_host.append(sv.Request(rid=200 + r.rid, kind="decode", params=r.params, image=alone["marked"],
+                                   nbits=inf["embedded"], b=inf["b"], lmr_map=alone.get("map_bits"),
+                                   lmr_eta=alone.get("eta_bits")))
+    in_state = srv.state.bytes
+    assert in_state > 0
+    out = {r.rid: r for r in srv.run(dec_state, realtime=False)}
+    for a, b in zip(dec_state, dec_host):
+        ra = out[a.rid].result
+        rb = sv.Server().run([b], realtime=False)[0].result
+        assert torch.equal(ra["bits"], rb["bits"]) and torch.equal(ra["recovered"], rb["recovered"]), a.rid
+        if a.params.variant == rd.LMR:
+            assert np.array_equal(ra["recovered"].numpy(), enc[a.rid - 100].image.numpy())
+    # the store is charged to the admission budget and can be emptied
+    for r in enc:
+        h = done[r.rid].result.get("state")
+        if h:
+            srv.drop_state(h)
+    assert srv.state.bytes == 0 and srv.ex.state_bytes() == 0

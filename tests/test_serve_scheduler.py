@@ -296,3 +296,38 @@ def test_idle_wait_does_not_spin():
     s.run(reqs, realtime=True)
     assert time.process_time() - c0 < 0.04
     assert all(r.status == "ok" for r in reqs)
+
+
+def test_admission_window_batches_arrivals_while_busy():
+    """With an admission window, requests that arrive while a batch is on the device wait
+    (up to the window) and leave together; an idle device takes a request at once."""
+    ex = FakeExecutor(slots=2, delay=lambda reqs: 0.02)
+    reqs = _reqs(12, spacing=0.001)
+    s = Scheduler(ex, max_batch=16, admit_window_ms=8.0)
+    s.run(reqs, realtime=True)
+    _check_terminal(s, reqs, ex)
+    assert ex.launched[0] == [0]                      # the idle device took the first request alone
+    assert max(len(b) for b in ex.launched) >= 4
+    assert len(ex.launched) <= 5
+    # no window: a free slot takes whatever is queued
+    ex2 = FakeExecutor(slots=2, delay=lambda reqs: 0.02)
+    s2 = Scheduler(ex2, max_batch=16)
+    s2.run(_reqs(12, spacing=0.001), realtime=True)
+    assert len(ex2.launched) >= len(ex.launched)
+
+
+def test_held_state_counts_against_the_budget():
+    """Device-resident state of earlier requests (reported by the executor) shrinks the
+    admission budget: with the budget almost all held, one request runs at a time."""
+    reqs = _reqs(6)
+    one = reqs[0].device_bytes()
+
+    class Holding(FakeExecutor):
+        def state_bytes(self):
+            return 10 * one
+
+    ex = Holding(slots=4)
+    s = Scheduler(ex, budget_bytes=11.5 * one, max_batch=8)
+    s.run(reqs, realtime=False)
+    _check_terminal(s, reqs, ex)
+    assert ex.max_live == 1 and all(len(b) == 1 for b in ex.launched)
