@@ -418,8 +418,10 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the public API with host buffers: H2D inputs, four calls,
     # D2H results, every step
-    e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec, wave_cols)
-    ceilings = measure_ceilings(rd, torch, dev, local_rank)
+    e2e = ceilings = None
+    if not args.kernels_only:
+        e2e = run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_np, pay_np, rec, wave_cols)
+        ceilings = measure_ceilings(rd, torch, dev, local_rank)
 
     clocks = clk.summary()
     return {"value": value, "total_ms": total_ms, "K": K, "per_stage": per_stage, "K_breakdown": K2,
@@ -1007,7 +1009,8 @@ def roofline(res, peaks, args):
     ks_bytes = {"pass1_keystream_hist": px, "pass1_keystream_decrypt": px,
                 "z2_encrypt_count": der / 8 * px, "z2_decrypt": der / 8 * px,
                 "enc_gather_embed": der / 8 * px, "extract_strips": der / 8 * px}
-    ceil = res["ceilings"]
+    ceil = res["ceilings"] or {"alu_tops": float("nan"), "keystream_gbs": float("nan"), "how": "not measured",
+                               "clocks": None}
     alu_peak = ceil["alu_tops"] * 1e12                            # measured ALU-pipe ops/s
     ks_peak = ceil["keystream_gbs"] * 1e9                         # measured keystream bytes/s
     hbm_peak = peaks.get("hbm_gbs", 6777.0)
@@ -1085,64 +1088,88 @@ def measured_traffic(kernel: str, px_per_launch: int):
     return None if k is None else k["dram_bytes_per_px"] * px_per_launch
 
 
-# ncu kernel name -> stage name, for the kernels of the traffic capture
-TRAFFIC_KERNELS = {"k_pass1<0, 0, 0>": "pass1_keystream_hist", "k_enc_rows<1, 0>": "enc_gather",
-                   "k_scan<0>": "embed_scan", "k_scan<1>": "extract_scan",
-                   "k_pass1<1, 0, 0>": "pass1_keystream_decrypt", "k_dec_strip<1, 0>": "dec_gather_recover"}
-TRAFFIC_CAPTURE = ('ncu --set full --clock-control none -k regex:"k_pass1|k_enc_rows|k_scan|k_dec_strip" -c 8 '
-                   '-o prof_full600 python bench.py --images 600 --steps 3 --warmup 3 --no-cpu-baseline')
+# ncu kernel name -> stage name, for the kernels of the traffic captures (fused path)
+TRAFFIC_KERNELS = {"k_pass1<0, 0, 0>": "pass1_keystream_hist", "k_enc_fused<1, 0>": "enc_gather_embed",
+                   "k_pass1<1, 0, 0>": "pass1_keystream_decrypt", "k_extract_strips": "extract_strips",
+                   "k_dec_strip<1, 0>": "dec_gather_recover", "k_topmap": "topmap_strips"}
+TRAFFIC_METRICS = ("dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum,"
+                   "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active,"
+                   "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active,"
+                   "sm__issue_active.avg.pct_of_peak_sustained_elapsed,"
+                   "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed,"
+                   "sm__warps_active.avg.pct_of_peak_sustained_active,launch__registers_per_thread,"
+                   "smsp__inst_executed.sum,smsp__inst_executed_pipe_alu.sum,"
+                   "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")
+# one capture per kernel on a 600-image batch: its launch in the first warm-up step of the
+# fused path, after `skip` earlier launches of the same function (the separable owner call
+# that sizes the payloads runs k_pass1<0> and k_topmap first; the receiver's k_pass1<1>
+# follows the owner's k_pass1<0> in the step)
+TRAFFIC_WORKLOAD = "python bench.py --images 600 --steps 1 --warmup 3 --kernels-only"
+TRAFFIC_SKIP = {"k_pass1<0, 0, 0>": 1, "k_pass1<1, 0, 0>": 2, "k_topmap": 1}
+TRAFFIC_CAPTURE = {k: (f'ncu --metrics {TRAFFIC_METRICS} --clock-control none -k regex:"{k.split("<")[0]}" '
+                       f'-s {TRAFFIC_SKIP.get(k, 0)} -c 1 --csv --page raw --log-file raw_{v}.csv {TRAFFIC_WORKLOAD}')
+                   for k, v in TRAFFIC_KERNELS.items()}
 
 
-def traffic_from_csv(csv_path: str, out_path: str, images: int = 600, size: int = 512) -> dict:
-    """Per-pixel DRAM traffic and pipe counters of the captured kernels, from the raw page
-    of an ncu report (`ncu -i prof_full600.ncu-rep --page raw --csv > raw.csv`) of
-    TRAFFIC_CAPTURE, written with the current kernel source hash."""
+def traffic_from_csv(csv_paths, out_path: str, images: int = 600, size: int = 512) -> dict:
+    """Per-pixel DRAM traffic and pipe counters of the captured kernels, from the raw
+    pages (`--csv --page raw`) of the per-kernel captures in TRAFFIC_CAPTURE, written
+    with the current kernel source hash."""
     import csv
-    with open(csv_path) as f:
-        rows = list(csv.reader(f))
-    head, units, data = rows[0], rows[1], rows[2:]
-    col = {name: i for i, name in enumerate(head)}
-    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "ms": 1e3}
-
-    def num(r, metric):
-        return float(r[col[metric]]) * scale.get(units[col[metric]], 1.0)
-
-    def short(name):
-        name = name.replace("void ", "")
-        return name[:name.index("(")] if "(" in name else name
-
+    if isinstance(csv_paths, str):
+        csv_paths = [csv_paths]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1.0, "ms": 1e3,
+             "usecond": 1.0, "nsecond": 1e-3, "msecond": 1e3}
     px = images * size * size
     groups = {}
-    for r in data:
-        stage = TRAFFIC_KERNELS.get(short(r[col["Kernel Name"]]))
-        if stage is not None:
-            groups.setdefault(stage, []).append(r)
+    for path in csv_paths:
+        with open(path) as f:
+            rows = [r for r in csv.reader(f) if r]
+        i0 = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+        head, units, data = rows[i0], rows[i0 + 1], rows[i0 + 2:]
+        col = {name: i for i, name in enumerate(head)}
+
+        def num(r, metric, col=col, units=units):
+            return float(r[col[metric]].replace(",", "")) * scale.get(units[col[metric]], 1.0)
+
+        def short(name):
+            name = name.replace("void ", "").replace("rdhei::", "")
+            return name[:name.index("(")] if "(" in name else name
+
+        for r in data:
+            name = short(r[col["Kernel Name"]])
+            stage = TRAFFIC_KERNELS.get(name)
+            if stage is not None:
+                groups.setdefault(stage, []).append((r, num, name))
     kernels = {}
     for stage, rs in groups.items():
         n = len(rs)
-        rd_b = sum(num(r, "dram__bytes_read.sum") for r in rs) / n
-        wr_b = sum(num(r, "dram__bytes_write.sum") for r in rs) / n
-        first = rs[0]
+        rd_b = sum(f(r, "dram__bytes_read.sum") for r, f, _ in rs) / n
+        wr_b = sum(f(r, "dram__bytes_write.sum") for r, f, _ in rs) / n
+        r0, f, name = rs[0]
         kernels[stage] = {
-            "kernel": short(first[col["Kernel Name"]]), "launches_captured": n,
+            "kernel": name, "launches_captured": n,
             "dram_bytes_per_px": (rd_b + wr_b) / px, "read_per_px": rd_b / px, "write_per_px": wr_b / px,
-            "us_600": sum(num(r, "gpu__time_duration.sum") for r in rs) / n,
-            "alu_pipe_pct": num(first, "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
-            "fma_pipe_pct": num(first, "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"),
-            "issue_pct": num(first, "sm__issue_active.avg.pct_of_peak_sustained_elapsed"),
-            "dram_pct": num(first, "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
-            "warps_active_pct": num(first, "sm__warps_active.avg.pct_of_peak_sustained_active"),
-            "regs": int(num(first, "launch__registers_per_thread")),
-            "inst_per_px": num(first, "smsp__inst_executed.sum") / px,
-            "tensor_pipe_pct": num(first, "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")}
-    doc = {"about": f"DRAM traffic per pixel of each kernel from one `ncu --set full` capture of a {images}-image "
-                    f"{size}x{size} batch; bench.py scales it to its 1000-image launches (traffic grows with the "
-                    "pixel count: every kernel streams whole images) and reports it only while the sources of the "
-                    "timed path's kernels hash to source_hash. Written by `python bench.py --traffic-from raw.csv`.",
-           "source_hash": kernel_source_hash(), "command": TRAFFIC_CAPTURE, "pixels_per_launch": px,
+            "us_600": sum(g(r, "gpu__time_duration.sum") for r, g, _ in rs) / n,
+            "alu_pipe_pct": f(r0, "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active"),
+            "fma_pipe_pct": f(r0, "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active"),
+            "issue_pct": f(r0, "sm__issue_active.avg.pct_of_peak_sustained_elapsed"),
+            "dram_pct": f(r0, "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed"),
+            "warps_active_pct": f(r0, "sm__warps_active.avg.pct_of_peak_sustained_active"),
+            "regs": int(f(r0, "launch__registers_per_thread")),
+            "inst_per_px": f(r0, "smsp__inst_executed.sum") * 32 / px,
+            "alu_inst_per_px": f(r0, "smsp__inst_executed_pipe_alu.sum") * 32 / px,
+            "tensor_pipe_pct": f(r0, "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active")}
+    doc = {"about": f"DRAM traffic and pipe counters per pixel of each kernel of the fused path, one ncu capture "
+                    f"per kernel (its first launch) on a {images}-image {size}x{size} batch; bench.py scales the "
+                    "traffic to its 1000-image launches (it grows with the pixel count: every kernel streams whole "
+                    "images) and reports it only while the sources of the timed path's kernels hash to "
+                    "source_hash.  inst_per_px counts thread instructions (warp instructions x 32).  Written by "
+                    "`python bench.py --traffic-from raw_*.csv`.",
+           "source_hash": kernel_source_hash(), "commands": TRAFFIC_CAPTURE, "pixels_per_launch": px,
            "kernels": kernels}
-    with open(out_path, "w") as f:
-        json.dump(doc, f, indent=1)
+    with open(out_path, "w") as fo:
+        json.dump(doc, fo, indent=1)
     return doc
 
 
@@ -1182,9 +1209,12 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4)
     ap.add_argument("--reference-budget", type=float, default=45.0,
                     help="--impl reference: seconds of oracle work over all its steps")
-    ap.add_argument("--traffic-from", metavar="RAW_CSV",
-                    help="write profiles/dram_traffic_batch600x512.json from the raw ncu page of the traffic "
-                         "capture and exit (no GPU needed)")
+    ap.add_argument("--traffic-from", metavar="RAW_CSV", nargs="+",
+                    help="write profiles/dram_traffic_batch600x512.json from the raw ncu pages of the per-kernel "
+                         "traffic captures and exit (no GPU needed)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time the step only: no oracle baseline, end-to-end leg, ceiling probes or serving leg "
+                         "(for profiler captures)")
     ap.add_argument("--path", default="fused", choices=["fused", "separable"],
                     help="fused: rdhei_encode (owner + hider) and rdhei_decode (both keys), 9 kernels a step; "
                          "separable: the four calls of the paper's parties, 17 kernels a step")
@@ -1238,7 +1268,7 @@ def main():
             print(json.dumps(run_stats(args) if args.config == "stats" else run_lmr_blocks(args)))
         return
     cpu_base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernels_only:
         cpu_base = oracle_throughput(args._images, 0, budget_s=10.0, med=args.med)
 
     if world > 1:
@@ -1248,7 +1278,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_gpu(args, rank, world, local_rank)
     serving = None
-    if world == 1 and args.serve_seconds > 0:
+    if world == 1 and args.serve_seconds > 0 and not args.kernels_only:
         # bounded serving leg: request latency of the continuous-batching server
         sres, n_pool = serving_runs(args, [(1.0, 1.0, False), (1.0, args.serve_seconds, True)], pool_n=48)
         serving = serving_summary(sres["x1"], args.serve_seconds, args.c5_rate, n_pool, args.c5_window_ms)

@@ -337,6 +337,15 @@ typedef struct rdhei_side_unpack_job {
     uint8_t *map_bits;        /* out: rot(l_b), ceil(H * W / 8) bytes */
 } rdhei_side_unpack_job;
 
+/* Eq. optimal_b as an ordered list, for an owner's fit loop that moves to the "next
+ * most optimal" b when its compressed maps do not fit (Sec. III-B-1): the candidate b
+ * (EMR 2..7, LMR 2..8) by decreasing capacity -- b * zeros(b) for EMR, (b - 1) *
+ * zeros(b) for LMR, zeros(b) = sum over t >= b of hist[t] (rdhei_info.hist) -- ties to
+ * the smaller b; order[0] is the b that rdhei_label_encrypt chooses with job.b = 0.
+ * HOST function.  Returns the number of candidates (6 or 7), or -1 for a null pointer
+ * or a bad variant. */
+int rdhei_b_candidates(const uint32_t hist[9], int variant, int32_t order[7], uint64_t capacity[7]);
+
 int rdhei_bilevel_encode(const uint8_t *bits, int H, int W, uint8_t *out, size_t cap, size_t *len);
 int rdhei_bilevel_decode(const uint8_t *in, size_t len, int H, int W, uint8_t *bits);
 int rdhei_lmr_side_pack(rdhei_side_pack_job *jobs, int n, int threads);
@@ -359,9 +368,13 @@ size_t rdhei_side_unpack_job_size(void);
  *     RDHEI_ESPACE before any GPU work.
  *   First call on a device: looks the array's device address up (cudaGetSymbolAddress
  *     with that device current) and caches it; make it before any stream capture.
+ *   Stream capture: a call on a stream that is being captured returns RDHEI_EINVAL
+ *     and enqueues nothing (each call uploads its descriptor from a host stack buffer).
  *   Sharing: every call uses the same array and it keeps the last call's contents;
  *     what must start at zero is cleared on each call.  Calls whose work overlaps on
  *     the GPU (other streams, other threads) race: order them on one stream.
+ *   Device-side errors (the checked build's index checks) reach info->status, which
+ *     the call's last kernel sets (0 when none).
  *   Returns RDHEI_EINVAL for bad arguments, RDHEI_ECUDA for a failed CUDA call. */
 #define RDHEI_NOALLOC_MAX_PIXELS (1u << 24)
 int rdhei_extract_noalloc(const rdhei_job *job, void *stream);

@@ -452,8 +452,9 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
 // ChaCha20 block per thread) into shared memory before the gather starts, while its
 // first loads are in flight; a strip whose message range does not fit is encrypted
 // chunk by chunk instead.  Per chunk: the strip's pixels come back from L2 (written
-// moments ago by this CTA), a block scan places each thread's slots and spread_slots
-// writes them.
+// moments ago by this CTA; the next chunk is not prefetched: its registers would cost
+// the fifth resident CTA per SM), a block scan places each thread's slots
+// and spread_slots writes them.
 constexpr int STRIP_WORDS = 4096;        // staged message words of one strip (131072 slot bits)
 struct EmbedSmem {
   uint32_t ebuf[STRIP_WORDS + 1];
@@ -525,11 +526,9 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
   const uint32_t slots = (uint32_t)slots_of(d, info);
   const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
   uint64_t Gc = r.G0;
-  ChunkPx cur;
-  load_run(d, d.dst, p0 + (uint64_t)HIDE_PX * t, p1, true, cur);
   for (uint64_t c0 = p0; c0 < p1 && Gc < r.send; c0 += SCAN_PX) {
-    ChunkPx nxt;                                             // next chunk in flight
-    load_run(d, d.dst, c0 + SCAN_PX + (uint64_t)HIDE_PX * t, p1, true, nxt);
+    ChunkPx cur;
+    load_run(d, d.dst, c0 + (uint64_t)HIDE_PX * t, p1, true, cur);
     const uint32_t zmask = zero_mask(d, cur);
     uint32_t Tc;
     const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, sm.warp_tot, Tc);
@@ -560,15 +559,15 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
       if (!staged) __syncthreads();   // the chunk's message words are rewritten by the next chunk
     }
     Gc += Tc;
-    cur = nxt;
   }
 }
 
 // Fused owner + hider (Sec. III-A-1 then III-A-2; III-B-1 then III-B-2): one CTA per
 // 64-row strip of the rotated image gathers, labels, rotates and encrypts its tiles
-// (as k_enc_rows) and then embeds the payload into that strip.
+// (as k_enc_rows) and then embeds the payload into that strip.  Five CTAs per SM
+// (48 registers) measured faster than four (64) or six (40, more spills).
 template <bool ANY_LMR, bool ANY_MED>
-__global__ void __launch_bounds__(256, 4) k_enc_fused(Batch B) {
+__global__ void __launch_bounds__(256, 5) k_enc_fused(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   __shared__ EncSmem<ANY_LMR, ANY_MED> sm;

@@ -10,7 +10,10 @@
 // caches it; make that first call before any stream capture.  All calls share the one
 // array and it keeps the last call's contents: the parts that must start at zero are
 // cleared on every call, and calls whose work overlaps on the GPU race on the array.
-// The kernels are the ones rdhei_extract launches (hide.cu).
+// The kernels are the ones rdhei_extract launches (hide.cu); a last one-thread kernel
+// copies the array's device error word into info->status.  A call on a stream that is
+// being captured is refused: the descriptor it uploads lives on the host stack.
+#include <atomic>
 #include <cstring>
 
 #include "../../include/rdhei.h"
@@ -39,7 +42,13 @@ static_assert(sizeof(ImgDesc) <= kPrefixOff - kDescOff, "descriptor does not fit
 __device__ __align__(256) uint8_t g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+// device address of the array per device; host threads may race on the first call of a
+// device, and every one of them stores the same address
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
+
+// the device error word of the call (index checks of the checked build) into the
+// image's info->status
+__global__ void k_noalloc_status(const uint32_t* err, rdhei_info* info) { info->status = (int32_t)*err; }
 
 struct Upload {
   ImgDesc d;
@@ -66,15 +75,18 @@ extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   if (j.max_bits && (!j.bits_out || (reinterpret_cast<uintptr_t>(j.bits_out) & 3))) return RDHEI_EINVAL;
   if ((j.variant & 1) == RDHEI_LMR && (!j.map_bits || (reinterpret_cast<uintptr_t>(j.map_bits) & 3))) return RDHEI_EINVAL;
 
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return RDHEI_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return RDHEI_EINVAL;   // the upload below reads a stack buffer
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RDHEI_ECUDA;
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return RDHEI_ECUDA;
-    g_scratch_ptr[dev] = p;
+  void* sp = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!sp) {
+    if (cudaGetSymbolAddress(&sp, g_scratch) != cudaSuccess || !sp) return RDHEI_ECUDA;
+    g_scratch_ptr[dev].store(sp, std::memory_order_release);
   }
-  uint8_t* base = static_cast<uint8_t*>(g_scratch_ptr[dev]);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* base = static_cast<uint8_t*>(sp);
 
   Upload up;
   std::memset(&up, 0, sizeof(up));
@@ -114,5 +126,6 @@ extern "C" int rdhei_extract_noalloc(const rdhei_job* job, void* stream) {
   launch_count(B, true, st);
   launch_scan(B, true, st);
   launch_z2_xor(B, true, st);
+  k_noalloc_status<<<1, 1, 0, st>>>(B.err, j.info);
   return cudaGetLastError() == cudaSuccess ? RDHEI_OK : RDHEI_ECUDA;
 }

@@ -291,3 +291,28 @@ extern "C" int rdhei_msb_plane(const uint8_t* src, int H, int W, uint8_t* out_bi
 
 extern "C" size_t rdhei_side_pack_job_size(void) { return sizeof(rdhei_side_pack_job); }
 extern "C" size_t rdhei_side_unpack_job_size(void) { return sizeof(rdhei_side_unpack_job); }
+
+// Eq. optimal_b as an ordered candidate list (the owner's fit loop walks it when the
+// compressed maps of its first choice do not fit): capacity b * zeros(b) (EMR) or
+// (b - 1) * zeros(b) (LMR), zeros(b) = sum over t >= b of hist[t]; decreasing capacity,
+// ties to the smaller b.  Insertion sort of at most seven entries.
+extern "C" int rdhei_b_candidates(const uint32_t hist[9], int variant, int32_t order[7], uint64_t capacity[7]) {
+  if (!hist || !order || !capacity || variant < RDHEI_EMR || variant > RDHEI_LMR_MED) return -1;
+  const bool lmr = (variant & 1) == RDHEI_LMR;
+  const int bmax = lmr ? 8 : 7;
+  int n = 0;
+  for (int b = 2; b <= bmax; b++) {
+    uint64_t zeros = 0;
+    for (int t = b; t <= 8; t++) zeros += hist[t];
+    const uint64_t cap = (uint64_t)(lmr ? b - 1 : b) * zeros;
+    int k = n++;
+    while (k > 0 && capacity[k - 1] < cap) {          // earlier (smaller) b wins ties: strict <
+      capacity[k] = capacity[k - 1];
+      order[k] = order[k - 1];
+      k--;
+    }
+    capacity[k] = cap;
+    order[k] = b;
+  }
+  return n;
+}

@@ -578,6 +578,21 @@ def _host_u8(a, nbytes=None):
     return a
 
 
+_lib.rdhei_b_candidates.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_uint64)]
+_lib.rdhei_b_candidates.restype = ctypes.c_int
+
+
+def b_candidates(hist, variant: int) -> list[tuple[int, int]]:
+    """(b, capacity) pairs in the order of Eq. optimal_b (rdhei_b_candidates)."""
+    h = (ctypes.c_uint32 * 9)(*[int(v) for v in hist])
+    order, cap = (ctypes.c_int32 * 7)(), (ctypes.c_uint64 * 7)()
+    n = _lib.rdhei_b_candidates(h, int(variant), order, cap)
+    if n < 0:
+        raise RdheiError("rdhei_b_candidates rejected its arguments")
+    return [(int(order[k]), int(cap[k])) for k in range(n)]
+
+
 def bilevel_encode(bits, H: int, W: int) -> bytes:
     """Compress H * W packed bits (host) with the library's bi-level coder."""
     import numpy as np

@@ -30,12 +30,10 @@ import torch
 from . import rdhei as rd
 
 
-def candidate_order(hist) -> list[int]:
-    """b = 2..8 by decreasing (b - 1) zeros(b), ties to the smaller b (Eq. optimal_b),
-    zeros(b) = pixels whose multi-MSB label is at least b."""
-    hist = [int(h) for h in hist]
-    zeros = {b: sum(hist[b:9]) for b in range(2, 9)}
-    return sorted(range(2, 9), key=lambda b: (-(b - 1) * zeros[b], b))
+def candidate_order(hist) -> list[tuple[int, int]]:
+    """(b, capacity) for b = 2..8 in the order of Eq. optimal_b for LMR, from the
+    library (rdhei_b_candidates)."""
+    return rd.b_candidates(hist, rd.LMR)
 
 
 @dataclass
@@ -68,7 +66,7 @@ def lmr_encode(imgs: list[torch.Tensor], params: list[rd.Params], threads: int =
     map_h = [x.cpu().numpy() for x in maps]
     cur = [0] * n                                   # index into order[i]
     b_now = [r["b"] for r in inf]
-    assert all(order[i][0] == b_now[i] for i in range(n))
+    assert all(order[i][0][0] == b_now[i] for i in range(n))
     done: dict[int, dict] = {}
     todo = list(range(n))
     while todo:
@@ -79,7 +77,7 @@ def lmr_encode(imgs: list[torch.Tensor], params: list[rd.Params], threads: int =
                 done[i] = r
             elif r["status"] == rd.RDHEI_ECAPACITY and cur[i] + 1 < len(order[i]):
                 cur[i] += 1
-                b_now[i] = order[i][cur[i]]
+                b_now[i] = order[i][cur[i]][0]
                 retry.append(i)
             elif r["status"] == rd.RDHEI_ECAPACITY:
                 done[i] = None                      # bad case
@@ -108,10 +106,9 @@ def lmr_encode(imgs: list[torch.Tensor], params: list[rd.Params], threads: int =
     for i in range(n):
         r = done[i]
         b = b_now[i] if r is not None else 0
-        zeros_b = sum(int(h) for h in inf[i]["hist"][b:9]) if b else 0
         out.append(LmrEncoded(b=b, enc=enc[i], map_bits=maps[i], eta_bits=etas[i],
                               side_nbits=r["side_nbits"] if r is not None else 0,
-                              capacity=(b - 1) * zeros_b if b else 0, tries=cur[i] + 1))
+                              capacity=order[i][cur[i]][1] if b else 0, tries=cur[i] + 1))
     return out
 
 

@@ -18,6 +18,8 @@ SUBSET = [
     ("tests/test_gpu_parity.py", "not c1_full_size"),
     ("tests/test_gpu_med.py", "shapes or edge or mixed or widths"),
     ("tests/test_gpu_configs.py", "uneven or mixed_variants"),
+    ("tests/test_gpu_fused.py", "shapes or partial or equals_separable"),
+    ("tests/test_zz_no_alloc.py", "twice or largest or side_stream"),
 ]
 
 

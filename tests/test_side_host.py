@@ -144,3 +144,30 @@ def test_block_size_sweep_has_the_printed_shape():
             vals.append(got)
         der[lmin] = float(np.mean(vals))
     assert der[4] >= der[1] > 0
+
+
+def test_b_candidates_match_the_oracle_order():
+    """rdhei_b_candidates (the fit loop's order of Eq. optimal_b) against the oracle:
+    LMR order and capacities (b - 1) zeros(b) from the oracle's histogram, the first
+    candidate equal to the oracle's choice of b for both variants, ties and empty
+    histograms included."""
+    import oracle
+    rd = _rd()
+    rng = np.random.default_rng(8)
+    hists = [np.zeros(9, np.int64), np.array([5, 0, 0, 0, 0, 0, 0, 0, 0]), np.array([0, 0, 6, 0, 3, 0, 2, 0, 0]),
+             np.array([0, 0, 0, 0, 0, 0, 0, 0, 9])]
+    for k in range(40):
+        img = synth.synth_image(int(rng.integers(8, 80)), int(rng.integers(8, 80)), 900 + k,
+                                noise_sigma=float(rng.uniform(0.5, 20)))
+        hists.append(oracle.label_hist(img).astype(np.int64))
+    for h in hists:
+        lmr = rd.b_candidates(h, rd.LMR)
+        assert [b for b, _ in lmr] == sc.candidate_order(h)
+        assert all(c == (b - 1) * int(h[b:].sum()) for b, c in lmr)
+        assert lmr[0][0] == oracle.choose_b(oracle.LMR, h.astype(np.uint32))
+        emr = rd.b_candidates(h, rd.EMR)
+        assert [b for b, _ in emr][0] == oracle.choose_b(oracle.EMR, h.astype(np.uint32))
+        assert sorted(b for b, _ in emr) == list(range(2, 8))
+        assert all(c == b * int(h[b:].sum()) for b, c in emr)
+        caps = [c for _, c in emr]
+        assert caps == sorted(caps, reverse=True)

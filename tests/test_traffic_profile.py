@@ -12,12 +12,15 @@ METRICS = ["dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.
            "sm__issue_active.avg.pct_of_peak_sustained_elapsed",
            "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed",
            "sm__warps_active.avg.pct_of_peak_sustained_active", "launch__registers_per_thread",
-           "smsp__inst_executed.sum", "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active"]
-UNITS = ["Mbyte", "Kbyte", "us", "%", "%", "%", "%", "%", "register/thread", "inst", "%"]
+           "smsp__inst_executed.sum", "smsp__inst_executed_pipe_alu.sum",
+           "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active"]
+UNITS = ["Mbyte", "Kbyte", "us", "%", "%", "%", "%", "%", "register/thread", "inst", "inst", "%"]
 
 
-def _write_csv(path, rows):
+def _write_csv(path, rows, preamble=()):
     with open(path, "w", newline="") as f:
+        for line in preamble:                 # ncu's log lines before the table
+            f.write(line + "\n")
         w = csv.writer(f)
         w.writerow(["ID", "Kernel Name"] + METRICS)
         w.writerow(["", ""] + UNITS)
@@ -25,28 +28,40 @@ def _write_csv(path, rows):
             w.writerow(r)
 
 
-def test_converter_scales_and_averages(tmp_path):
-    src = tmp_path / "raw.csv"
-    _write_csv(src, [
-        ["0", "void k_pass1<0, 0, 0>(Batch)", "100", "500", "160", "84", "27", "75", "21", "53", "56", "4000", "0"],
-        ["1", "void k_pass1<0, 0, 0>(Batch)", "300", "700", "170", "86", "27", "75", "21", "53", "56", "4000", "0"],
-        ["2", "void k_enc_rows<1, 0>(Batch, unsigned int)", "20", "10", "150", "64", "15", "63", "38", "70", "40",
-         "800", "0"],
-        ["3", "void k_topmap(Batch, int)", "1", "1", "5", "1", "1", "1", "1", "1", "30", "10", "0"],
+def test_converter_merges_captures_scales_and_averages(tmp_path):
+    a, b = tmp_path / "raw_a.csv", tmp_path / "raw_b.csv"
+    _write_csv(a, [
+        ["0", "void rdhei::k_pass1<0, 0, 0>(rdhei::Batch)", "100", "500", "160", "84", "27", "75", "21", "53", "56",
+         "4000", "3000", "0"],
+        ["1", "void rdhei::k_pass1<0, 0, 0>(rdhei::Batch)", "300", "700", "170", "86", "27", "75", "21", "53", "56",
+         "4000", "3000", "0"],
+        ["3", "void rdhei::k_zero(uint4 *, unsigned int)", "1", "1", "5", "1", "1", "1", "1", "1", "30", "10", "1",
+         "0"],
+    ], preamble=["==PROF== Connected to process 1"])
+    _write_csv(b, [
+        ["0", "void rdhei::k_enc_fused<1, 0>(rdhei::Batch)", "20", "10", "150", "64", "15", "63", "38", "70", "64",
+         "800", "500", "0"],
     ])
     out = tmp_path / "t.json"
-    doc = bench.traffic_from_csv(str(src), str(out), images=2, size=10)
+    doc = bench.traffic_from_csv([str(a), str(b)], str(out), images=2, size=10)
     px = 2 * 10 * 10
     k = doc["kernels"]
-    assert set(k) == {"pass1_keystream_hist", "enc_gather"}              # uncaptured kernels ignored
+    assert set(k) == {"pass1_keystream_hist", "enc_gather_embed"}        # uncaptured kernels ignored
     p = k["pass1_keystream_hist"]
     assert p["launches_captured"] == 2 and p["kernel"] == "k_pass1<0, 0, 0>"
     assert p["read_per_px"] == 200e6 / px and p["write_per_px"] == 600e3 / px    # Mbyte, Kbyte
     assert p["dram_bytes_per_px"] == (200e6 + 600e3) / px
-    assert p["us_600"] == 165.0 and p["regs"] == 56 and p["inst_per_px"] == 4000 / px
-    assert k["enc_gather"]["kernel"] == "k_enc_rows<1, 0>"
+    assert p["us_600"] == 165.0 and p["regs"] == 56
+    assert p["inst_per_px"] == 4000 * 32 / px and p["alu_inst_per_px"] == 3000 * 32 / px   # warp -> thread
+    assert k["enc_gather_embed"]["kernel"] == "k_enc_fused<1, 0>"
     assert doc["source_hash"] == bench.kernel_source_hash()
     assert json.loads(out.read_text()) == doc
+
+
+def test_capture_recipe_is_one_small_capture_per_kernel():
+    for kernel, cmd in bench.TRAFFIC_CAPTURE.items():
+        assert "--clock-control none" in cmd and " -c 1 " in cmd and " -s " in cmd and "--set full" not in cmd
+        assert kernel.split("<")[0] in cmd and "--kernels-only" in cmd and "--images 600" in cmd
 
 
 def test_stale_profile_gives_no_traffic(tmp_path, monkeypatch):
