@@ -444,7 +444,7 @@ def run_e2e(args, rd, torch, dev, world, imgs_np, variants, params, caps, side_n
     sn = side_nbits(H, W)
     lmr = [(v & 1) == rd.LMR for v in variants]
     op = pp.OverlappedPipeline(n, H, W, variants, params, caps, side_nbits=[sn if l else 0 for l in lmr],
-                               chunks=args.e2e_chunks, device=dev, wave_cols=wave_cols)
+                               chunks=args.e2e_chunks, device=dev, wave_cols=wave_cols, fused=args.path == "fused")
     h_img, h_pay, h_side, h_rec, h_bits = op.host_buffers()
     h_img.copy_(torch.from_numpy(imgs_np))
     op.pack_payloads(h_pay, [pay_np[k] for k in range(n)])
@@ -576,8 +576,9 @@ def run_c3(args):
         kk = synth.keys(seeds[k])
         params.append(rd.Params(variant=variants[k], k1=kk["k1"], nonce1=kk["nonce1"], k2=kk["k2"], nonce2=kk["nonce2"]))
     torch.cuda.set_device(0)
+    fused = args.path == "fused"
     s = pp.ImageSet(imgs, variants, params)
-    bp = pp.BatchedPipeline(s, pp.default_payload(lambda i: seeds[i]))
+    bp = pp.BatchedPipeline(s, pp.default_payload(lambda i: seeds[i]), fused=fused)
     px = s.pixels()
 
     def timed(fn, K):
@@ -597,7 +598,7 @@ def run_c3(args):
     ref_rec = [x.clone() for x in s.rec]
     ref_bits = [x.clone() for x in s.bits]
     ms_batched = timed(bp.step, args.steps)
-    pi = pp.PerImagePipeline(s)
+    pi = pp.PerImagePipeline(s, fused=fused)
     for x in s.rec:
         x.zero_()
     ms_per_image = timed(pi.step, max(3, args.steps // 4))
@@ -608,7 +609,8 @@ def run_c3(args):
             "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"uneven batch: {args.c3_small} images with H, W drawn from {list(C3_SIDES)} "
-                                   f"+ {args.c3_big} x 8192x8192, EMR/LMR alternating, full-capacity payload",
+                                   f"+ {args.c3_big} x 8192x8192, EMR/LMR alternating, full-capacity payload, "
+                                   + ("rdhei_encode + rdhei_decode" if fused else "the four separable calls"),
                        "pixels": px},
             "batching": {"graph_batched_mpx": px / (ms_graph / 1e3) / 1e6,
                          "eager_batched_mpx": px / (ms_batched / 1e3) / 1e6,
@@ -751,9 +753,11 @@ def run_c4(args):
                          info=info[k], b=0) for k in range(n)], st).run(rd.OP_EMBED, st)
     del enc
     bits = torch.zeros((n, pb), dtype=torch.uint8, device=dev)
-    p_ext = rd.Plan([rd.make_job(params[k], H, W, src=marked[k], bits_out=bits[k], max_bits=caps[k], info=info[k],
-                                 b=0) for k in range(n)], st)
-    dec_jobs = [rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], info=info[k], b=0) for k in range(n)]
+    fused = args.path == "fused"
+    p_ext = None if fused else rd.Plan([rd.make_job(params[k], H, W, src=marked[k], bits_out=bits[k],
+                                                    max_bits=caps[k], info=info[k], b=0) for k in range(n)], st)
+    dec_jobs = [rd.make_job(params[k], H, W, src=marked[k], dst=rec[k], info=info[k], b=0,
+                            **({"bits_out": bits[k], "max_bits": caps[k]} if fused else {})) for k in range(n)]
     tuning = None
     wave_cols = None
     if args.med:
@@ -762,9 +766,12 @@ def run_c4(args):
         wave_cols, times = tune.best_wave_cols(dec_jobs, st)
         tuning = {"wave_cols": wave_cols, "ms_per_width": times}
     p_dec = rd.Plan(dec_jobs, st, wave_cols=wave_cols)
-    stages = [(p_ext, rd.OP_EXTRACT, i, rd.stages(rd.OP_EXTRACT)[i]) for i in p_ext.active_stages(rd.OP_EXTRACT)] + \
-             [(p_dec, rd.OP_DECRYPT_RECOVER, i, rd.stages(rd.OP_DECRYPT_RECOVER)[i])
-              for i in p_dec.active_stages(rd.OP_DECRYPT_RECOVER)]
+    if fused:
+        stages = [(p_dec, rd.OP_DECODE, i, rd.stages(rd.OP_DECODE)[i]) for i in p_dec.active_stages(rd.OP_DECODE)]
+    else:
+        stages = [(p_ext, rd.OP_EXTRACT, i, rd.stages(rd.OP_EXTRACT)[i]) for i in p_ext.active_stages(rd.OP_EXTRACT)] \
+            + [(p_dec, rd.OP_DECRYPT_RECOVER, i, rd.stages(rd.OP_DECRYPT_RECOVER)[i])
+               for i in p_dec.active_stages(rd.OP_DECRYPT_RECOVER)]
     for _ in range(args.warmup):
         for pl, op, i, _ in stages:
             pl.run_stage(op, i, st)
@@ -787,10 +794,11 @@ def run_c4(args):
     der = float(np.mean(caps)) / N
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6777.0)
-    # compulsory bytes of the two calls: extract reads I_e' and writes DER/8 B of bits,
-    # decrypt_recover reads I_e' and writes I'
-    algo = (3.0 + der / 8) * n * N
+    # compulsory bytes: the fused decode reads I_e' once and writes I' and DER/8 B of bits;
+    # the two separable calls each read I_e'
+    algo = ((2.0 if fused else 3.0) + der / 8) * n * N
     out_extra = {"tuning": tuning} if tuning else {}
+    out_extra["path"] = "rdhei_decode" if fused else "rdhei_extract + rdhei_decrypt_recover"
     return {**out_extra, "metric": "Mpixel/s decode (extract + decrypt_recover, bit-exact)", "value": n * N / (ms / 1e3) / 1e6,
             "unit": "Mpixel/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -801,7 +809,8 @@ def run_c4(args):
             "per_stage_ms": per, "algorithmic_gbs": algo / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm,
             "algorithmic_hbm_frac": algo / (ms / 1e3) / 1e9 / hbm,
             "recovery_lsb_only": exact, "payload_roundtrip": bits_ok, "clocks": clk.summary(),
-            "gpu_launches": len(stages) * K}
+            # stages, plus each operation's zero-region kernel and the separable extractor's offsets kernel
+            "gpu_launches": (len(stages) + (1 if fused else 3)) * K}
 
 
 # ---------------------------------------------------------- security stats --
@@ -1212,6 +1221,8 @@ def main():
     ap.add_argument("--traffic-from", metavar="RAW_CSV", nargs="+",
                     help="write profiles/dram_traffic_batch600x512.json from the raw ncu pages of the per-kernel "
                          "traffic captures and exit (no GPU needed)")
+    ap.add_argument("--no-config-legs", action="store_true",
+                    help="skip the short uneven-batch (c3) and decode-stress (c4) runs of the default line")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time the step only: no oracle baseline, end-to-end leg, ceiling probes or serving leg "
                          "(for profiler captures)")
@@ -1277,6 +1288,27 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_gpu(args, rank, world, local_rank)
+    configs = None
+    if world == 1 and not args.kernels_only and not args.no_config_legs:
+        # short runs of the uneven-batch and decode-stress workloads, recorded beside the headline
+        import copy
+        a2 = copy.copy(args)
+        a2.steps, a2.warmup = 10, 3
+        c3 = run_c3(a2)
+        c4 = run_c4(a2)
+        configs = {
+            "uneven_batch": {"gpx_s_graph": c3["batching"]["graph_batched_mpx"] / 1e3,
+                             "gpx_s_eager": c3["batching"]["eager_batched_mpx"] / 1e3,
+                             "gpx_s_per_image_plans": c3["batching"]["per_image_plain_mpx"] / 1e3,
+                             "launches_batched": c3["batching"]["launches_batched"],
+                             "launches_per_image": c3["batching"]["launches_per_image"],
+                             "outputs_equal": c3["batching"]["outputs_equal"],
+                             "lmr_lossless": c3["batching"]["lmr_lossless"], "ms_per_step": c3["ms_per_step"],
+                             "workload": c3["config"]["workload"]},
+            "decode_stress": {"gpx_s": c4["value"] / 1e3, "ms_per_step": c4["ms_per_step"],
+                              "algorithmic_hbm_frac": c4["algorithmic_hbm_frac"], "per_stage_ms": c4["per_stage_ms"],
+                              "recovery_lsb_only": c4["recovery_lsb_only"], "payload_roundtrip": c4["payload_roundtrip"],
+                              "clocks": c4["clocks"], "workload": c4["config"]["workload"]}}
     serving = None
     if world == 1 and args.serve_seconds > 0 and not args.kernels_only:
         # bounded serving leg: request latency of the continuous-batching server
@@ -1301,6 +1333,8 @@ def main():
         line["tuning"] = res["tuning"]
     if serving is not None:
         line["serving"] = serving
+    if configs is not None:
+        line["configs"] = configs
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -448,23 +448,22 @@ __global__ void __launch_bounds__(256, ANY_MED ? 5 : 6) k_enc_rows(Batch B, uint
 // Hider's half of the fused encode (Sec. III-A-2 / III-B-2) for one 64-row strip of
 // the rotated image that this CTA has just encrypted: its slots start at stream bit
 // strip_base (k_topmap), so the 8192-pixel chunks are walked in raster order with a
-// running offset.  The strip's message words are K2-encrypted (e = m XOR z2, one
-// ChaCha20 block per thread) into shared memory before the gather starts, while its
-// first loads are in flight; a strip whose message range does not fit is encrypted
-// chunk by chunk instead.  Per chunk: the strip's pixels come back from L2 (written
-// moments ago by this CTA; the next chunk is not prefetched: its registers would cost
-// the fifth resident CTA per SM), a block scan places each thread's slots
-// and spread_slots writes them.
-constexpr int STRIP_WORDS = 4096;        // staged message words of one strip (131072 slot bits)
+// running offset.  The message words are K2-encrypted (e = m XOR z2) into a window of
+// shared memory, one ChaCha20 block per thread: the strip's first window while the
+// gather's first loads are in flight, the next one whenever a chunk's slots run past
+// it (wide strips).  Per chunk: the strip's pixels come back from L2 (written moments
+// ago by this CTA; the next chunk is not prefetched: its registers would cost the
+// fifth resident CTA per SM), a block scan places each thread's slots and spread_slots
+// writes them.
+constexpr int WINDOW_WORDS = 16 * 255;   // message words staged at once: at most 256 ChaCha20 blocks
 struct EmbedSmem {
-  uint32_t ebuf[STRIP_WORDS + 1];
+  uint32_t ebuf[WINDOW_WORDS + 1];
   uint32_t warp_tot[HIDE_THREADS / 32];
   SlotTables tabs;
-  int staged;
 };
 
 // e words [w_lo, w_lo + nw) of image d's message into buf (MSB-first), and a zero word
-// after them; one ChaCha20 block of z2 per thread, nblk <= HIDE_THREADS blocks
+// after them; one ChaCha20 block of z2 per thread (nw <= WINDOW_WORDS: <= 256 blocks)
 __device__ __forceinline__ void stage_message(const ImgDesc& d, uint64_t w_lo, uint32_t nw, uint32_t* buf) {
   const int t = threadIdx.x;
   const uint64_t j0 = w_lo >> 4;
@@ -492,21 +491,17 @@ __device__ __forceinline__ StripRange strip_range(const Batch& B, uint32_t s, co
   return {G0, umin64(G0 + B.strip_tot[s], info->embedded)};
 }
 
-// the whole strip's message words, when they fit (called while phase 1's loads fly)
+// the window of message words that starts at stream word w0: up to WINDOW_WORDS, not
+// past the strip's last slot
+__device__ __forceinline__ uint32_t window_words(uint64_t w0, uint64_t send) {
+  return (uint32_t)umin64(WINDOW_WORDS, ((send - 1) >> 5) - w0 + 1);
+}
+
+// the strip's first window (called while phase 1's loads fly)
 __device__ __forceinline__ void stage_strip(const Batch& B, uint32_t s, EmbedSmem& sm) {
   const ImgDesc& d = B.desc[__ldg(B.strip_owner + s)];
   const StripRange r = strip_range(B, s, d);
-  int staged = 0;
-  if (r.send > r.G0) {
-    const uint64_t W0 = r.G0 >> 5, W1 = (r.send - 1) >> 5;
-    const uint32_t nw = (uint32_t)(W1 - W0 + 1);
-    const uint32_t nblk = (uint32_t)((W1 >> 4) - (W0 >> 4) + 1);
-    if (nw <= (uint32_t)STRIP_WORDS && nblk <= (uint32_t)HIDE_THREADS) {
-      stage_message(d, W0, nw, sm.ebuf);
-      staged = 1;
-    }
-  }
-  if (threadIdx.x == 0) sm.staged = staged;
+  if (r.send > r.G0) stage_message(d, r.G0 >> 5, window_words(r.G0 >> 5, r.send), sm.ebuf);
 }
 
 __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSmem& sm) {
@@ -519,34 +514,35 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
   const uint64_t W = (uint64_t)d.W;
   const uint64_t p0 = (uint64_t)ty * TILE * W, p1 = (uint64_t)min((int)(ty + 1) * TILE, d.H) * W;
   const StripRange r = strip_range(B, s, d);
-  __syncthreads();   // tables; the staged flag and message (written before phase 1's first barrier)
+  __syncthreads();   // tables; the first window (written before phase 1's first barrier)
   if (r.G0 >= r.send) return;
-  const bool staged = sm.staged != 0;
-  const uint64_t W0 = r.G0 >> 5;
+  uint64_t Wb = r.G0 >> 5;                                   // the staged window: words [Wb, Wb + Wn)
+  uint32_t Wn = window_words(Wb, r.send);
   const uint32_t slots = (uint32_t)slots_of(d, info);
   const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
   uint64_t Gc = r.G0;
   for (uint64_t c0 = p0; c0 < p1 && Gc < r.send; c0 += SCAN_PX) {
     ChunkPx cur;
-    load_run(d, d.dst, c0 + (uint64_t)HIDE_PX * t, p1, true, cur);
+    const uint64_t q0 = c0 + (uint64_t)HIDE_PX * t;
+    load_run(d, d.dst, q0, p1, true, cur);
     const uint32_t zmask = zero_mask(d, cur);
     uint32_t Tc;
     const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, sm.warp_tot, Tc);
     const uint64_t endc = umin64(Gc + Tc, r.send);
     if (endc > Gc) {
       const uint64_t w_lo = Gc >> 5;
-      const uint32_t* sbuf = sm.ebuf + (w_lo - W0);
-      if (!staged) {
-        // message words of this chunk's slot range only
-        const uint32_t nw = (uint32_t)(((endc - 1) >> 5) - w_lo + 1);
-        if (RDHEI_IDX_OK(B.err, nw < (uint32_t)SBUF_WORDS)) stage_message(d, w_lo, nw, sm.ebuf);
-        sbuf = sm.ebuf;
+      if (((endc - 1) >> 5) >= Wb + Wn) {
+        // the chunk's slots run past the window: the next window starts at its first word
+        // (the block scan's barriers ordered every earlier read of the buffer)
+        Wb = w_lo;
+        Wn = window_words(Wb, r.send);
+        stage_message(d, Wb, Wn, sm.ebuf);
         __syncthreads();
       }
       const uint64_t k0 = Gc + my_off;
       if (zmask && k0 < endc) {
-        spread_slots(cur.px, zmask, slots, fshift, sbuf, 32 * w_lo, k0, endc, sm.tabs, B.err);
-        uint8_t* dst = d.dst + (c0 + (uint64_t)HIDE_PX * t);
+        spread_slots(cur.px, zmask, slots, fshift, sm.ebuf + (w_lo - Wb), 32 * w_lo, k0, endc, sm.tabs, B.err);
+        uint8_t* dst = d.dst + q0;
         if (cur.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
           __stcg(reinterpret_cast<uint4*>(dst), make_uint4(cur.px[0], cur.px[1], cur.px[2], cur.px[3]));
           __stcg(reinterpret_cast<uint4*>(dst) + 1, make_uint4(cur.px[4], cur.px[5], cur.px[6], cur.px[7]));
@@ -556,7 +552,6 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
             if (k < cur.valid) dst[k] = (uint8_t)(cur.px[k >> 2] >> (8 * (k & 3)));
         }
       }
-      if (!staged) __syncthreads();   // the chunk's message words are rewritten by the next chunk
     }
     Gc += Tc;
   }

@@ -246,15 +246,15 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
 // the both-keys decode): one CTA per 64-row strip of the marked image.  The strip's
 // slots start at the stream bit k_topmap derived from per-tile label counts, so the
 // CTA walks its 8192-pixel chunks in raster order with a running offset -- no count
-// pass, no cross-CTA wait.  The K2 keystream of the strip's message words is computed
-// once, one ChaCha20 block per thread, while the first chunk's loads are in flight (a
-// strip whose range does not fit the buffer computes it chunk by chunk).  Each chunk's
-// slots are gathered into shared memory, XOR-ed with the keystream and stored: words
-// inside the chunk's range whole, words shared with a neighbouring chunk or strip with
-// atomicOr into words that start at zero (cleared by k_topmap at strip ends, here at
-// chunk ends).
-constexpr int Z2_STRIP_WORDS = 16 * HIDE_THREADS;   // 256 keystream blocks
-static_assert(Z2_STRIP_WORDS >= Z2BUF_WORDS, "the strip buffer also holds one chunk's keystream");
+// pass, no cross-CTA wait.  The K2 keystream is staged in a window of up to 256
+// ChaCha20 blocks, one block per thread: the strip's first window while the first
+// chunk's loads are in flight, the next one whenever a chunk's output words run past
+// it (wide strips).  Each chunk's slots are gathered into shared memory, XOR-ed with
+// the keystream and stored: words inside the chunk's range whole, words shared with a
+// neighbouring chunk or strip with atomicOr into words that start at zero (cleared by
+// k_topmap at strip ends, here at chunk ends).
+constexpr int Z2_WINDOW_BLOCKS = HIDE_THREADS;   // 256 keystream blocks = 4096 words
+static_assert(16 * Z2_WINDOW_BLOCKS >= Z2BUF_WORDS, "a window holds one chunk's keystream");
 
 // keystream words of blocks [j0, j0 + nblk) into z2 (one block per thread)
 __device__ __forceinline__ void z2_blocks(const ImgDesc& d, uint64_t j0, uint32_t nblk, uint32_t* z2) {
@@ -267,11 +267,17 @@ __device__ __forceinline__ void z2_blocks(const ImgDesc& d, uint64_t j0, uint32_
   }
 }
 
+// blocks of the window that starts at block j0: up to Z2_WINDOW_BLOCKS, not past the
+// block of the strip's last slot
+__device__ __forceinline__ uint32_t z2_window(uint64_t j0, uint64_t send) {
+  return (uint32_t)umin64(Z2_WINDOW_BLOCKS, (((send - 1) >> 5) >> 4) - j0 + 1);
+}
+
 __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   __shared__ uint32_t sbuf[SBUF_WORDS];
-  __shared__ uint32_t z2buf[Z2_STRIP_WORDS];
+  __shared__ uint32_t z2buf[16 * Z2_WINDOW_BLOCKS];
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
   __shared__ SlotTables tabs;
   const int t = threadIdx.x;
@@ -293,11 +299,10 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   (void)out_words;                                           // index checks only
   ChunkPx cur;
   load_run(d, d.src, p0 + (uint64_t)HIDE_PX * t, p1, false, cur);
-  // the strip's keystream, while the first chunk's loads are in flight
-  const uint64_t J0 = (G0 >> 5) >> 4;
-  const uint32_t nblkS = (uint32_t)((((send - 1) >> 5) >> 4) - J0 + 1);
-  const bool staged = nblkS <= (uint32_t)HIDE_THREADS;
-  if (staged) z2_blocks(d, J0, nblkS, z2buf);
+  // the strip's first keystream window, while the first chunk's loads are in flight
+  uint64_t Jb = (G0 >> 5) >> 4;                              // window: blocks [Jb, Jb + Jn)
+  uint32_t Jn = z2_window(Jb, send);
+  z2_blocks(d, Jb, Jn, z2buf);
   __syncthreads();   // tables, keystream
   uint64_t Gc = G0;
   for (uint64_t c0 = p0; c0 < p1 && Gc < send; c0 += SCAN_PX) {
@@ -310,10 +315,12 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
     if (endc > Gc) {
       for (int i = t; i < (int)((Tc >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
       const uint64_t wa = Gc >> 5, wb = (endc - 1) >> 5;
-      uint64_t zbase = 16 * J0;                              // word index of z2buf[0]
-      if (!staged) {
-        zbase = 16 * (wa >> 4);
-        z2_blocks(d, wa >> 4, (uint32_t)((wb >> 4) - (wa >> 4) + 1), z2buf);
+      if ((wb >> 4) >= Jb + Jn) {
+        // the chunk's words run past the window: the next window starts at its first block
+        // (the block scan's barriers ordered every earlier read of z2buf)
+        Jb = wa >> 4;
+        Jn = z2_window(Jb, send);
+        z2_blocks(d, Jb, Jn, z2buf);
       }
       // a word that starts inside this chunk and ends inside the next one of this strip
       // is cleared here, before the ORs of both; the word holding the strip's end (shared
@@ -324,11 +331,12 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
       __syncthreads();
       gather_slots(cur.px, zmask, slots, fshift, my_off, sbuf, tabs, B.err);
       __syncthreads();
+      const uint64_t zbase = 16 * Jb;                        // word index of z2buf[0]
       for (uint64_t w = wa + t; w <= wb; w += HIDE_THREADS) {
         const uint64_t b0 = 32 * w;
         const uint64_t lo = b0 > Gc ? b0 : Gc, hi = b0 + 32 < endc ? b0 + 32 : endc;   // my bits of word w
         if (!RDHEI_IDX_OK(B.err, w < out_words && ((lo - Gc) >> 5) + 1 < SBUF_WORDS &&
-                                     w - zbase < (uint64_t)Z2_STRIP_WORDS))
+                                     w - zbase < (uint64_t)(16 * Z2_WINDOW_BLOCKS)))
           continue;
         const uint32_t raw = get_bits(sbuf, (uint32_t)(lo - Gc), (uint32_t)(hi - lo)) << (uint32_t)(b0 + 32 - hi);
         const uint32_t keep = (0xFFFFFFFFu >> (uint32_t)(lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (uint32_t)(hi - b0));
@@ -336,7 +344,6 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
         if (lo == b0 && hi == b0 + 32) out[w] = v;
         else atomicOr(out + w, v);
       }
-      __syncthreads();   // sbuf (and an unstaged keystream) are rewritten by the next chunk
     }
     Gc += Tc;
     cur = nxt;

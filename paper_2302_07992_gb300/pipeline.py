@@ -1,7 +1,9 @@
 """Batched pipelines over the C ABI: a fixed set of images (any sizes, both variants)
-with their device buffers and the four plans, run eagerly or replayed as one captured
-CUDA graph, plus the per-image form (one plan per image and operation) it is compared
-against.  Argument marshalling and buffer management only -- all work is in the
+with their device buffers and one plan per operation, run eagerly or replayed as one
+captured CUDA graph, plus the per-image form (one plan per image and operation) it is
+compared against.  A round trip is either the four separable calls of the paper's
+parties or the two fused ones (rdhei_encode: owner + hider; rdhei_decode: receiver with
+both keys).  Argument marshalling and buffer management only -- all work is in the
 library's kernels.
 """
 from __future__ import annotations
@@ -13,6 +15,7 @@ from . import rdhei as rd
 from . import synth
 
 OPS = (rd.OP_LABEL_ENCRYPT, rd.OP_EMBED, rd.OP_EXTRACT, rd.OP_DECRYPT_RECOVER)
+FUSED_OPS = (rd.OP_ENCODE, rd.OP_DECODE)
 
 
 class ImageSet:
@@ -66,6 +69,14 @@ class ImageSet:
         if op == rd.OP_EXTRACT:
             return rd.make_job(p, H, W, src=self.marked[i], map_bits=self.maps[i], bits_out=self.bits[i],
                                max_bits=self.caps[i], info=self.info[i], b=0)
+        if op == rd.OP_ENCODE:
+            return rd.make_job(p, H, W, src=self.img[i], dst=self.marked[i], map_bits=self.maps[i],
+                               eta_bits=self.etas[i], side_bits=self.side[i], side_nbits=self.side_n[i],
+                               payload=self.payload[i], nbits=self.caps[i], info=self.info[i])
+        if op == rd.OP_DECODE:
+            return rd.make_job(p, H, W, src=self.marked[i], dst=self.rec[i], map_bits=self.maps[i],
+                               eta_bits=self.etas[i], bits_out=self.bits[i], max_bits=self.caps[i],
+                               info=self.info[i], b=0)
         return rd.make_job(p, H, W, src=self.marked[i], dst=self.rec[i], map_bits=self.maps[i],
                            eta_bits=self.etas[i], info=self.info[i], b=0)
 
@@ -74,19 +85,22 @@ class ImageSet:
 
 
 class BatchedPipeline:
-    """One plan per operation over the whole set; a step is four plan runs, optionally
-    captured into a single CUDA graph."""
+    """One plan per operation over the whole set; a step is four plan runs (two with
+    fused=True), optionally captured into a single CUDA graph."""
 
-    def __init__(self, s: ImageSet, payload_fn, stream=None):
+    def __init__(self, s: ImageSet, payload_fn, stream=None, fused: bool = False):
         self.s = s
         stream = stream or torch.cuda.current_stream()
         enc = rd.Plan(s.encode_jobs(), stream)
-        enc.run(rd.OP_LABEL_ENCRYPT, stream)
+        enc.run(rd.OP_LABEL_ENCRYPT, stream)        # the capacities size the payloads
         torch.cuda.synchronize()
         s.set_payloads(payload_fn)
-        self.plans = [(enc, rd.OP_LABEL_ENCRYPT)]
-        for op in OPS[1:]:
-            self.plans.append((rd.Plan([s.job(op, i) for i in range(s.n)], stream), op))
+        if fused:
+            self.plans = [(rd.Plan([s.job(op, i) for i in range(s.n)], stream), op) for op in FUSED_OPS]
+        else:
+            self.plans = [(enc, rd.OP_LABEL_ENCRYPT)]
+            for op in OPS[1:]:
+                self.plans.append((rd.Plan([s.job(op, i) for i in range(s.n)], stream), op))
         self.graph = None
 
     def step(self, stream=None):
@@ -114,12 +128,14 @@ class BatchedPipeline:
 
 
 class PerImagePipeline:
-    """The plain form: every image runs its own four single-image plans."""
+    """The plain form: every image runs its own single-image plans (four, or two with
+    fused=True)."""
 
-    def __init__(self, s: ImageSet, stream=None):
+    def __init__(self, s: ImageSet, stream=None, fused: bool = False):
         self.s = s
         stream = stream or torch.cuda.current_stream()
-        self.plans = [[(rd.Plan([s.job(op, i)], stream), op) for op in OPS] for i in range(s.n)]
+        ops = FUSED_OPS if fused else OPS
+        self.plans = [[(rd.Plan([s.job(op, i)], stream), op) for op in ops] for i in range(s.n)]
 
     def step(self, stream=None):
         for per in self.plans:
@@ -142,10 +158,11 @@ class OverlappedPipeline:
     c - 2's results (recovered pixels, extracted bits) come down on a download stream.
     Events order the reuse of each chunk's device buffers from one run to the next.
     Payloads and extracted bits are packed per image to their capacity, so only the
-    bytes that carry bits cross the bus."""
+    bytes that carry bits cross the bus.  fused=True runs rdhei_encode and rdhei_decode
+    per chunk instead of the four separable calls."""
 
     def __init__(self, n, H, W, variants, params, caps, side_nbits=None, chunks=4, device="cuda", wave_cols=None,
-                 graphs=True):
+                 graphs=True, fused: bool = False):
         self.n, self.H, self.W = n, H, W
         self.dev = torch.device(device)
         N = H * W
@@ -197,6 +214,20 @@ class OverlappedPipeline:
                                        info=self.info[k], b=0))
                 dec.append(rd.make_job(p, H, W, src=self.marked[k], dst=self.rec[k], map_bits=m,
                                        eta_bits=self.etas[k] if lmr[k] else None, info=self.info[k], b=0))
+            if fused:
+                fenc = [rd.make_job(params[k], H, W, src=self.img[k], dst=self.marked[k],
+                                    map_bits=self.maps[k] if lmr[k] else None,
+                                    eta_bits=self.etas[k] if lmr[k] else None,
+                                    side_bits=self.side[self.side_off[k]:] if self.side_nbits[k] else None,
+                                    side_nbits=self.side_nbits[k], payload=self.pay[self.pay_off[k]:],
+                                    nbits=self.caps[k], info=self.info[k]) for k in range(a, b)]
+                fdec = [rd.make_job(params[k], H, W, src=self.marked[k], dst=self.rec[k],
+                                    map_bits=self.maps[k] if lmr[k] else None,
+                                    eta_bits=self.etas[k] if lmr[k] else None, bits_out=self.bits[self.pay_off[k]:],
+                                    max_bits=self.caps[k], info=self.info[k], b=0) for k in range(a, b)]
+                self.plans.append([(rd.Plan(fenc, self.comp), rd.OP_ENCODE),
+                                   (rd.Plan(fdec, self.comp, wave_cols=wave_cols), rd.OP_DECODE)])
+                continue
             self.plans.append([(rd.Plan(enc, self.comp), rd.OP_LABEL_ENCRYPT), (rd.Plan(emb, self.comp), rd.OP_EMBED),
                                (rd.Plan(ext, self.comp), rd.OP_EXTRACT),
                                (rd.Plan(dec, self.comp, wave_cols=wave_cols), rd.OP_DECRYPT_RECOVER)])

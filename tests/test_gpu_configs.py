@@ -176,9 +176,11 @@ def test_decode_only_on_oracle_marked_4096(rd):
         assert np.array_equal(rec.cpu().numpy(), rref)
 
 
-def test_overlapped_host_pipeline_matches_the_oracle():
+@pytest.mark.parametrize("fused", [False, True])
+def test_overlapped_host_pipeline_matches_the_oracle(fused):
     """Host-to-host runs with copies overlapped across chunks give each image's oracle
-    result, run after run (buffer reuse between runs is ordered by events)."""
+    result, run after run (buffer reuse between runs is ordered by events), through the
+    four separable calls or the two fused ones."""
     import torch
     from paper_2302_07992_gb300 import pipeline as pp
     from paper_2302_07992_gb300 import rdhei as rd
@@ -203,7 +205,7 @@ def test_overlapped_host_pipeline_matches_the_oracle():
         pays.append(pay)
         sides.append(side if lmr else np.zeros(1, np.uint8))
     op = pp.OverlappedPipeline(n, H, W, variants, params, caps,
-                               side_nbits=[sn if (v & 1) == rd.LMR else 0 for v in variants], chunks=3)
+                               side_nbits=[sn if (v & 1) == rd.LMR else 0 for v in variants], chunks=3, fused=fused)
     h_img, h_pay, h_side, h_rec, h_bits = op.host_buffers()
     h_img.copy_(torch.from_numpy(imgs))
     op.pack_payloads(h_pay, pays)
@@ -280,6 +282,56 @@ def test_repeated_steps_without_host_synchronisation(rd):
 
 
 
+def test_repeated_fused_steps_without_host_synchronisation(rd):
+    """The fused calls queued back to back three times over the same buffers with no host
+    synchronisation: the final outputs equal the oracle's."""
+    shapes = [(512, 512), (100, 130), (257, 333), (64, 1000), (700, 96)]
+    variants = [rd.EMR, rd.LMR, rd.EMR_MED, rd.LMR, rd.LMR_MED]
+    imgs = [synth.synth_image(H, W, 950 + i) for i, (H, W) in enumerate(shapes)]
+    seeds = [950 + i for i in range(len(shapes))]
+    n = len(imgs)
+    P = [rd.Params(variant=v, **_keys(s)) for v, s in zip(variants, seeds)]
+    d_img = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    scratch = [torch.empty_like(x) for x in d_img]
+    marked = [torch.empty_like(x) for x in d_img]
+    rec = [torch.empty_like(x) for x in d_img]
+    N = [im.size for im in imgs]
+    lmr = [(v & 1) == rd.LMR for v in variants]
+    maps = [rd.bitbuf(N[i]) for i in range(n)]
+    etas = [rd.bitbuf(N[i]) for i in range(n)]
+    info = rd.new_info(n)
+    st = torch.cuda.current_stream()
+    rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=d_img[i], dst=scratch[i], info=info[i]) for i in range(n)],
+            st).run(rd.OP_LABEL_ENCRYPT, st)
+    torch.cuda.synchronize()
+    caps = [r["capacity"] for r in rd.read_info(info)]
+    pays = [synth.payload_bits(seeds[i], caps[i]) for i in range(n)]
+    d_pay = [rd.as_bitbuf(torch.from_numpy(pays[i]), caps[i]) for i in range(n)]
+    bits = [rd.bitbuf(caps[i]) for i in range(n)]
+    lm = [maps[i] if lmr[i] else None for i in range(n)]
+    et = [etas[i] if lmr[i] else None for i in range(n)]
+    p_enc = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=d_img[i], dst=marked[i], map_bits=lm[i], eta_bits=et[i],
+                                 payload=d_pay[i], nbits=caps[i], info=info[i]) for i in range(n)], st)
+    p_dec = rd.Plan([rd.make_job(P[i], *imgs[i].shape, src=marked[i], dst=rec[i], map_bits=lm[i], eta_bits=et[i],
+                                 bits_out=bits[i], max_bits=caps[i], info=info[i], b=0) for i in range(n)], st)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        p_enc.run(rd.OP_ENCODE, st)
+        p_dec.run(rd.OP_DECODE, st)
+    torch.cuda.synchronize()
+    assert p_enc.status(st) == 0 and p_dec.status(st) == 0
+    for i in range(n):
+        op = oracle.Params(variant=variants[i], **_keys(seeds[i]))
+        r = oracle.label_encrypt(op, imgs[i])
+        l_np = r.map_bits if lmr[i] else None
+        mref, _ = oracle.embed(op, r.b, r.enc, pays[i], r.capacity, l_np)
+        assert np.array_equal(marked[i].cpu().numpy(), mref), i
+        xref, xk = oracle.extract(op, r.b, mref, r.capacity, l_np)
+        assert np.array_equal(_bits(bits[i], xk), xref), i
+        rref = oracle.decrypt_recover(op, r.b, mref, l_np, r.eta_bits if lmr[i] else None)
+        assert np.array_equal(rec[i].cpu().numpy(), rref), i
+
+
 def test_full_benchmark_batch_sampled(rd):
     """The benchmark's own workload and launch configuration -- 1000 synthetic 512 x 512
     images, EMR (even) / LMR (odd) with ceil(N/8) side bits, full-capacity payloads,
@@ -347,3 +399,30 @@ def test_full_benchmark_batch_sampled(rd):
         assert g["extracted"] == xk and np.array_equal(_bits(bits[k], xk), xref), k
         rref = oracle.decrypt_recover(op, r.b, mref, lm, r.eta_bits if lmr[k] else None)
         assert np.array_equal(rec[k].cpu().numpy(), rref), k
+
+    # the fused calls in the benchmark's launch configuration (one plan per call over the
+    # whole batch, jobs as bench.py builds them): every image equals the separable chain's
+    # output checked above
+    marked2, rec2 = torch.empty_like(imgs), torch.empty_like(imgs)
+    maps2 = torch.zeros_like(maps)
+    etas2 = torch.zeros_like(etas)
+    bits2 = torch.zeros_like(bits)
+    info2 = rd.new_info(n)
+    m2 = [maps2[k] if lmr[k] else None for k in range(n)]
+    pe = rd.Plan([rd.make_job(params[k], H, W, src=imgs[k], dst=marked2[k], map_bits=m2[k],
+                              eta_bits=etas2[k] if lmr[k] else None, side_bits=sides[k] if lmr[k] else None,
+                              side_nbits=sn if lmr[k] else 0, payload=payload[k], nbits=caps[k], info=info2[k])
+                  for k in range(n)])
+    pd = rd.Plan([rd.make_job(params[k], H, W, src=marked2[k], dst=rec2[k], map_bits=m2[k],
+                              eta_bits=etas2[k] if lmr[k] else None, bits_out=bits2[k], max_bits=caps[k],
+                              info=info2[k], b=0) for k in range(n)])
+    for _ in range(2):
+        pe.run(rd.OP_ENCODE)
+        pd.run(rd.OP_DECODE)
+    torch.cuda.synchronize()
+    assert pe.status() == 0 and pd.status() == 0
+    assert torch.equal(marked2, marked) and torch.equal(rec2, rec) and torch.equal(bits2, bits)
+    assert torch.equal(maps2, maps) and torch.equal(etas2, etas)
+    g2 = rd.read_info(info2)
+    assert all(g2[k]["embedded"] == caps[k] and g2[k]["extracted"] == caps[k] and g2[k]["b"] == got[k]["b"]
+               for k in range(n))
