@@ -593,6 +593,13 @@ def run_c3(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / K
 
+    tuning = None
+    if fused:
+        # rows per extraction CTA, tuned for this batch (cached per device and shape set)
+        from paper_2302_07992_gb300 import tune
+        rows, times = tune.best_extract_rows(bp.jobs(rd.OP_DECODE))
+        bp.plan(rd.OP_DECODE).set_param(rd.PARAM_EXTRACT_ROWS, rows)
+        tuning = {"extract_rows": rows, "ms_per_value": times}
     bp.capture()
     ms_graph = timed(bp.replay, args.steps)
     ref_rec = [x.clone() for x in s.rec]
@@ -616,7 +623,8 @@ def run_c3(args):
                          "eager_batched_mpx": px / (ms_batched / 1e3) / 1e6,
                          "per_image_plain_mpx": px / (ms_per_image / 1e3) / 1e6,
                          "launches_batched": bp.launches_per_step(), "launches_per_image": pi.launches_per_step(),
-                         "outputs_equal": bool(same), "lmr_lossless": bool(lossless)}}
+                         "outputs_equal": bool(same), "lmr_lossless": bool(lossless)},
+            "tuning": tuning}
 
 
 # ------------------------------------------------------------------ serving --
@@ -767,6 +775,10 @@ def run_c4(args):
         tuning = {"wave_cols": wave_cols, "ms_per_width": times}
     p_dec = rd.Plan(dec_jobs, st, wave_cols=wave_cols)
     if fused:
+        from paper_2302_07992_gb300 import tune
+        rows, times = tune.best_extract_rows(dec_jobs, st)
+        p_dec.set_param(rd.PARAM_EXTRACT_ROWS, rows)
+        tuning = {**(tuning or {}), "extract_rows": rows, "ms_per_value": times}
         stages = [(p_dec, rd.OP_DECODE, i, rd.stages(rd.OP_DECODE)[i]) for i in p_dec.active_stages(rd.OP_DECODE)]
     else:
         stages = [(p_ext, rd.OP_EXTRACT, i, rd.stages(rd.OP_EXTRACT)[i]) for i in p_ext.active_stages(rd.OP_EXTRACT)] \
@@ -1304,11 +1316,11 @@ def main():
                              "launches_per_image": c3["batching"]["launches_per_image"],
                              "outputs_equal": c3["batching"]["outputs_equal"],
                              "lmr_lossless": c3["batching"]["lmr_lossless"], "ms_per_step": c3["ms_per_step"],
-                             "workload": c3["config"]["workload"]},
+                             "tuning": c3.get("tuning"), "workload": c3["config"]["workload"]},
             "decode_stress": {"gpx_s": c4["value"] / 1e3, "ms_per_step": c4["ms_per_step"],
                               "algorithmic_hbm_frac": c4["algorithmic_hbm_frac"], "per_stage_ms": c4["per_stage_ms"],
                               "recovery_lsb_only": c4["recovery_lsb_only"], "payload_roundtrip": c4["payload_roundtrip"],
-                              "clocks": c4["clocks"], "workload": c4["config"]["workload"]}}
+                              "clocks": c4["clocks"], "tuning": c4.get("tuning"), "workload": c4["config"]["workload"]}}
     serving = None
     if world == 1 and args.serve_seconds > 0 and not args.kernels_only:
         # bounded serving leg: request latency of the continuous-batching server

@@ -225,6 +225,21 @@ int rdhei_plan_stage_active(const rdhei_plan *plan, int op, int stage);
  * changes the layout).  Returns RDHEI_EINVAL for another value or an uploaded plan. */
 int rdhei_plan_set_wave_cols(rdhei_plan *plan, int cols);
 
+/* Free launch parameters of a plan (the autotuner's knobs; results do not depend on them):
+ *   RDHEI_PARAM_EXTRACT_ROWS  rows of a 64-row strip that one rdhei_decode extraction CTA
+ *                             handles: 64, 32, 16, 8 or 4; 0 = chosen per batch (whole
+ *                             strips unless the batch has fewer than 8 strips per SM).
+ *                             Takes effect at the next run.
+ *   RDHEI_PARAM_ENC_SPLIT     CTAs that share one tile row of rdhei_label_encrypt's gather:
+ *                             1..64; 0 = chosen per batch (more for small batches).  Takes
+ *                             effect at the next run.
+ *   RDHEI_PARAM_WAVE_COLS     as rdhei_plan_set_wave_cols (before upload only).
+ * rdhei_plan_set_param returns RDHEI_EINVAL for an unknown parameter or value;
+ * rdhei_plan_get_param returns the value in effect (the chosen one for 0), -1 if unknown. */
+enum rdhei_param { RDHEI_PARAM_WAVE_COLS = 1, RDHEI_PARAM_EXTRACT_ROWS = 2, RDHEI_PARAM_ENC_SPLIT = 3 };
+int rdhei_plan_set_param(rdhei_plan *plan, int param, int value);
+int rdhei_plan_get_param(rdhei_plan *plan, int param);
+
 /* ---------------------------------------------------------------------------------
  * Security and quality statistics (Sec. IV-C, Tab. analysis; PSNR and SSIM of the
  * reconstructed image, Sec. IV) for a batch of 8-bit images:

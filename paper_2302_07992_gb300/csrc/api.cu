@@ -13,7 +13,7 @@ void launch_pass1(const Batch& B, int mode, bool general, bool any_med, cudaStre
 void launch_topmap(const Batch& B, bool owner, bool fused, cudaStream_t st);
 void launch_enc_fused(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 void launch_extract_strips(const Batch& B, cudaStream_t st);
-void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
+void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, uint32_t nsplit, cudaStream_t st);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 void launch_dec_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st);
 void launch_count(const Batch& B, bool extract, cudaStream_t st);
@@ -38,9 +38,12 @@ struct rdhei_plan {
          off_tile_flags = 0, off_desc = 0, off_tile_prefix = 0, off_chunk_prefix = 0, off_z2_prefix = 0, off_strip_prefix = 0, off_tile_rows = 0,
          off_subtree = 0, off_aux = 0, off_sigma6 = 0, off_tilemap = 0, off_wave_flags = 0, off_wave_list = 0,
          off_lab = 0, off_tile_owner = 0, off_strip_owner = 0, off_tile_cnt = 0, off_strip_base = 0,
-         off_strip_tot = 0, total = 0;
+         off_strip_tot = 0, off_rowcnt = 0, off_part_base = 0, total = 0;
   uint32_t total_tiles = 0, total_chunks = 0, total_z2 = 0, total_strips = 0, total_wave = 0;
   int wave_cols = WAVE_COLS_DEFAULT;
+  int extract_rows = 0;                  // rows per k_extract_strips CTA (0 = chosen per batch)
+  int auto_rows = 0;                     // the choice for 0, made once
+  int enc_split = 0;                     // k_enc_rows CTAs per tile row (0 = chosen per batch)
   bool any_lmr = false, general = false, any_med = false;
   void* ws = nullptr;
   Batch batch{};
@@ -157,6 +160,10 @@ static void build_layout(rdhei_plan* p) {
   off = align_up(off + (size_t)p->total_strips * 4, 256);
   p->off_strip_tot = off;
   off = align_up(off + (size_t)p->total_strips * 4, 256);
+  p->off_rowcnt = off;
+  off = align_up(off + (size_t)p->total_tiles * TILE, 256);
+  p->off_part_base = off;
+  off = align_up(off + (size_t)p->total_strips * MAX_PARTS * 4, 256);
   p->stash_off.resize(n);
   p->ebuf_off.resize(n);
   for (int i = 0; i < n; i++) {
@@ -317,6 +324,10 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.tile_cnt = reinterpret_cast<uint16_t*>(base + p->off_tile_cnt);
   B.strip_base = reinterpret_cast<uint32_t*>(base + p->off_strip_base);
   B.strip_tot = reinterpret_cast<uint32_t*>(base + p->off_strip_tot);
+  B.rowcnt = base + p->off_rowcnt;
+  B.part_base = reinterpret_cast<uint32_t*>(base + p->off_part_base);
+  B.part_rows = TILE;
+  B.count_rows = 0;
   return RDHEI_OK;
 }
 
@@ -372,6 +383,22 @@ static int check_op(const rdhei_plan* p, int op) {
   return RDHEI_OK;
 }
 
+// rows of a strip per extraction CTA: the plan's setting, else whole strips unless the
+// batch has too few strips to fill the GPU twice over (small batches, serving)
+static int extract_rows_of(rdhei_plan* p) {
+  if (p->extract_rows) return p->extract_rows;
+  if (p->auto_rows) return p->auto_rows;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+      cudaSuccess || sms <= 0)
+    sms = 152;
+  const uint64_t want = (uint64_t)sms * 8;
+  int rows = TILE;
+  while (rows > 4 && (uint64_t)p->total_strips * (TILE / rows) < want) rows >>= 1;
+  p->auto_rows = rows;
+  return rows;
+}
+
 int rdhei_plan_stage_count(int op) {
   switch (op) {
     case RDHEI_OP_DECODE:
@@ -415,7 +442,9 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
   if (stage < 0 || stage >= rdhei_plan_stage_count(op)) return RDHEI_EINVAL;
   NvtxRange range(rdhei_stage_name(op, stage));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const Batch& B = p->batch;
+  Batch B = p->batch;
+  B.part_rows = op == RDHEI_OP_DECODE ? extract_rows_of(p) : TILE;   // only the fused decode splits strips
+  B.count_rows = op == RDHEI_OP_DECODE ? 1 : 0;
   if (stage == 0) {
     int rc = check_op(p, op);
     if (rc) return rc;
@@ -437,7 +466,7 @@ int rdhei_plan_run_stage(rdhei_plan* p, int op, int stage, void* stream) {
     case RDHEI_OP_LABEL_ENCRYPT:
       if (stage == 0) launch_pass1(B, 0, p->general, p->any_med, st);
       else if (stage == 1) launch_topmap(B, true, false, st);
-      else launch_enc_pass2(B, p->any_lmr, p->any_med, st);
+      else launch_enc_pass2(B, p->any_lmr, p->any_med, (uint32_t)p->enc_split, st);
       break;
     case RDHEI_OP_EMBED:
       if (stage == 0) launch_z2_count(B, st);
@@ -493,6 +522,33 @@ int rdhei_plan_set_wave_cols(rdhei_plan* p, int cols) {
   if (layout_wave(p) != RDHEI_OK) return RDHEI_EINVAL;
   build_layout(p);
   return RDHEI_OK;
+}
+
+int rdhei_plan_set_param(rdhei_plan* p, int param, int value) {
+  if (!p) return RDHEI_EINVAL;
+  switch (param) {
+    case RDHEI_PARAM_WAVE_COLS:
+      return rdhei_plan_set_wave_cols(p, value);
+    case RDHEI_PARAM_EXTRACT_ROWS:
+      if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32 && value != 64) return RDHEI_EINVAL;
+      p->extract_rows = value;
+      return RDHEI_OK;
+    case RDHEI_PARAM_ENC_SPLIT:
+      if (value < 0 || value > 64) return RDHEI_EINVAL;
+      p->enc_split = value;
+      return RDHEI_OK;
+  }
+  return RDHEI_EINVAL;
+}
+
+int rdhei_plan_get_param(rdhei_plan* p, int param) {
+  if (!p) return -1;
+  switch (param) {
+    case RDHEI_PARAM_WAVE_COLS: return p->wave_cols;
+    case RDHEI_PARAM_EXTRACT_ROWS: return extract_rows_of(p);
+    case RDHEI_PARAM_ENC_SPLIT: return p->enc_split;
+  }
+  return -1;
 }
 
 int rdhei_plan_stage_active(const rdhei_plan* p, int op, int stage) {

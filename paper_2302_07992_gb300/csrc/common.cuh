@@ -131,7 +131,13 @@ struct Batch {
   uint16_t* tile_cnt;             // total_tiles * 8: label-0 pixels per tile (owner: b = 1..8; receiver: [0])
   uint32_t* strip_base;           // total_strips: first payload bit of each 64-row strip (fused calls)
   uint32_t* strip_tot;            // total_strips: payload bits of each strip (fused calls)
+  uint8_t* rowcnt;                // total_tiles * 64: label-0 pixels of each tile row (split strips)
+  uint32_t* part_base;            // total_strips * 16: first payload bit of each part of a strip
+  int32_t part_rows;              // fused decode: rows of a strip per extraction CTA (64, 32, .., 4)
+  int32_t count_rows;             // fused decode: the first pass writes rowcnt
 };
+
+constexpr int MAX_PARTS = 16;     // parts of a 64-row strip at 4 rows each
 
 // MED recovery wavefront tile: 32 rows (one warp lane per row) x wave_cols columns.
 constexpr int WAVE_ROWS = 32, WAVE_COLS_DEFAULT = 128;

@@ -29,8 +29,11 @@ constexpr int MAX_STRIPS = 1024;   // 64-row strips of the tallest image (H <= 6
 //             tiles through the tile map (a tile moves as a whole, and the in-tile
 //             rotation only permutes its pixels); the receiver's tiles are already in
 //             the rotated domain.  Owner: embedded = min(nbits, capacity); receiver:
-//             extracted = min(max_bits, capacity), and the output words that two strips
-//             share (and the last, partial one) are cleared for the extractor's ORs.
+//             extracted = min(max_bits, capacity), the first bit of each part when
+//             the extraction splits strips (rows B.part_rows at a time, from the first
+//             pass's per-tile-row counts), and the clearing of the output words that
+//             two strips or parts share (and of the last, partial one): the extractor
+//             writes those with atomicOr.
 __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner, int fused) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
@@ -145,7 +148,6 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner, int fused) {
       const uint32_t v = strip_acc[i] * slots;
       B.strip_base[sbase + i] = run;
       B.strip_tot[sbase + i] = v;
-      strip_acc[i] = run;                              // the strip's first bit, for the clearing below
       run += v;
     }
     if (lane == 0) {
@@ -159,12 +161,40 @@ __global__ void __launch_bounds__(256) k_topmap(Batch B, int owner, int fused) {
   }
   if (owner) return;
   __syncthreads();
-  // receiver: words of bits_out that two strips share, and the last partial word, start
-  // at zero (the extractor writes them with atomicOr)
   const uint64_t E = info->extracted;
   uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
-  for (uint32_t i = threadIdx.x + 1; i < ns; i += blockDim.x) {
-    const uint32_t G = strip_acc[i];
+  const int R = B.part_rows, parts = TILE / R;
+  if (parts > 1) {
+    // slots of each part (R rows of a strip), one warp per part: lanes take the strip's
+    // tiles, four row counts per 32-bit load (rows below the image count 0)
+    const uint32_t tiles_x = d.tiles_x, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (uint32_t e = threadIdx.x >> 5; e < ns * (uint32_t)parts; e += nwarps) {
+      const uint32_t st = e / parts, k = e - st * parts;
+      const uint32_t* rc = reinterpret_cast<const uint32_t*>(
+          B.rowcnt + ((size_t)d.tile_base + (size_t)st * tiles_x) * TILE + (size_t)k * R);
+      uint32_t c = 0;
+      for (uint32_t tx = lane; tx < tiles_x; tx += 32)
+        for (int q = 0; q < R / 4; q++) c = __dp4a(rc[(size_t)tx * (TILE / 4) + q], 0x01010101u, c);
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (lane == 0) B.part_base[(size_t)(sbase + st) * MAX_PARTS + k] = c * slots;
+    }
+    __syncthreads();
+    // within each strip: exclusive prefix from the strip's first bit; a part boundary
+    // inside a word clears that word
+    for (uint32_t st = threadIdx.x; st < ns; st += blockDim.x) {
+      uint32_t* pb = B.part_base + (size_t)(sbase + st) * MAX_PARTS;
+      uint64_t run = B.strip_base[sbase + st];
+      for (int k = 0; k < parts; k++) {
+        const uint32_t v = pb[k];
+        pb[k] = (uint32_t)run;
+        if (k > 0 && run < E && (run & 31u)) out[run >> 5] = 0u;
+        run += v;
+      }
+    }
+  }
+  // the words two strips share, and the last partial word
+  for (uint32_t st = threadIdx.x + 1; st < ns; st += blockDim.x) {
+    const uint64_t G = B.strip_base[sbase + st];
     if (G < E && (G & 31u)) out[G >> 5] = 0u;
   }
   if (threadIdx.x == 0 && (E & 31u)) out[E >> 5] = 0u;
@@ -588,16 +618,19 @@ void launch_enc_fused(const Batch& B, bool any_lmr, bool any_med, cudaStream_t s
     else launch_pdl(k_enc_fused<false, false>, grid, block, 0, st, B);
   }
 }
-void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, cudaStream_t st) {
+void launch_enc_pass2(const Batch& B, bool any_lmr, bool any_med, uint32_t nsplit, cudaStream_t st) {
   if (B.total_strips == 0) return;
   // whole tile rows per CTA (the next tile's fetch hides the current one's latency),
-  // split when the batch has fewer rows than ~4 CTAs per SM slot
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-  const uint32_t want = (uint32_t)sms * 6u * 4u;
-  uint32_t nsplit = want / B.total_strips;
-  nsplit = nsplit < 1 ? 1 : nsplit > 64 ? 64 : nsplit;
+  // split when the batch has fewer rows than ~4 CTAs per SM slot (unless the plan fixes
+  // the split)
+  if (nsplit == 0) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    const uint32_t want = (uint32_t)sms * 6u * 4u;
+    nsplit = want / B.total_strips;
+    nsplit = nsplit < 1 ? 1 : nsplit > 64 ? 64 : nsplit;
+  }
   const uint32_t grid = B.total_strips * nsplit;
   if (any_med) {
     if (any_lmr) launch_pdl(k_enc_rows<true, true>, dim3(grid), dim3(256), 0, st, B, nsplit);

@@ -243,16 +243,17 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
 }
 
 // Fused decode, K2 half (Sec. III-A-3 / III-B-3, "receiver has only K2", run inside
-// the both-keys decode): one CTA per 64-row strip of the marked image.  The strip's
-// slots start at the stream bit k_topmap derived from per-tile label counts, so the
-// CTA walks its 8192-pixel chunks in raster order with a running offset -- no count
-// pass, no cross-CTA wait.  The K2 keystream is staged in a window of up to 256
-// ChaCha20 blocks, one block per thread: the strip's first window while the first
-// chunk's loads are in flight, the next one whenever a chunk's output words run past
-// it (wide strips).  Each chunk's slots are gathered into shared memory, XOR-ed with
-// the keystream and stored: words inside the chunk's range whole, words shared with a
-// neighbouring chunk or strip with atomicOr into words that start at zero (cleared by
-// k_topmap at strip ends, here at chunk ends).
+// the both-keys decode): one CTA per part of a 64-row strip of the marked image (rows
+// B.part_rows at a time; a whole strip by default).  Each part's slots start at the
+// stream bit k_topmap derived from label counts of the first pass (per tile, or per
+// tile row for split strips), so the CTA walks its 8192-pixel chunks in raster order
+// with a running offset -- no count pass, no cross-CTA wait.  The K2 keystream is
+// staged in a window of up to 256 ChaCha20 blocks, one block per thread: the first
+// window while the first chunk's loads are in flight, the next one whenever a chunk's
+// output words run past it (wide strips).  Each chunk's slots are gathered into shared
+// memory, XOR-ed with the keystream and stored: words inside the chunk's range whole,
+// words shared with a neighbouring chunk or CTA with atomicOr into words that start at
+// zero (cleared by k_topmap at part and strip ends, here at chunk ends).
 constexpr int Z2_WINDOW_BLOCKS = HIDE_THREADS;   // 256 keystream blocks = 4096 words
 static_assert(16 * Z2_WINDOW_BLOCKS >= Z2BUF_WORDS, "a window holds one chunk's keystream");
 
@@ -282,17 +283,26 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   __shared__ SlotTables tabs;
   const int t = threadIdx.x;
   init_slot_tables(tabs);
-  const uint32_t s = blockIdx.x;
+  const uint32_t R = (uint32_t)B.part_rows, parts = TILE / R;
+  const uint32_t s = blockIdx.x / parts, part = blockIdx.x % parts;
   const int img = (int)__ldg(B.strip_owner + s);
   const ImgDesc& d = B.desc[img];
   const rdhei_info* info = reinterpret_cast<const rdhei_info*>(d.info);
   const uint32_t ty = s - __ldg(B.strip_prefix + img);
   const uint64_t W = (uint64_t)d.W;
-  const uint64_t p0 = (uint64_t)ty * TILE * W, p1 = (uint64_t)min((int)(ty + 1) * TILE, d.H) * W;
-  const uint64_t G0 = B.strip_base[s];
-  const uint64_t send = umin64(G0 + B.strip_tot[s], info->extracted);
-  if (G0 >= send) return;                                    // uniform: no slots to read
+  const uint32_t rows = (uint32_t)min(TILE, d.H - (int)ty * TILE);
+  const uint32_t r0 = part * R, r1 = min(r0 + R, rows);
+  if (r0 >= rows) return;                                    // uniform: the strip has no such rows
   const uint32_t slots = (uint32_t)slots_of(d, info);
+  uint64_t G0 = B.strip_base[s], Gend = G0 + B.strip_tot[s];
+  if (parts > 1) {
+    const uint32_t* pb = B.part_base + (size_t)s * MAX_PARTS;
+    G0 = pb[part];
+    if (r1 < rows) Gend = pb[part + 1];                      // else the strip's end
+  }
+  const uint64_t p0 = ((uint64_t)ty * TILE + r0) * W, p1 = ((uint64_t)ty * TILE + r1) * W;
+  const uint64_t send = umin64(Gend, info->extracted);
+  if (G0 >= send) return;                                    // uniform: no slots to read
   const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
   uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
   const uint64_t out_words = (d.max_bits + 31) >> 5;
@@ -322,9 +332,9 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
         Jn = z2_window(Jb, send);
         z2_blocks(d, Jb, Jn, z2buf);
       }
-      // a word that starts inside this chunk and ends inside the next one of this strip
-      // is cleared here, before the ORs of both; the word holding the strip's end (shared
-      // with the next strip, or the last one) was cleared by k_topmap
+      // a word that starts inside this chunk and ends inside the next one of this part
+      // is cleared here, before the ORs of both; the word holding the part's end (shared
+      // with the next part or strip, or the last one) was cleared by k_topmap
       if (t == 0 && (endc & 31) && ((endc >> 5) << 5) >= Gc && (endc >> 5) < (send >> 5) &&
           RDHEI_IDX_OK(B.err, (endc >> 5) < out_words))
         out[endc >> 5] = 0u;
@@ -470,7 +480,7 @@ void launch_z2_xor(const Batch& B, bool decrypt, cudaStream_t st) {
 }
 void launch_extract_strips(const Batch& B, cudaStream_t st) {
   if (B.total_strips == 0) return;
-  launch_pdl(k_extract_strips, dim3(B.total_strips), dim3(HIDE_THREADS), 0, st, B);
+  launch_pdl(k_extract_strips, dim3(B.total_strips * (TILE / B.part_rows)), dim3(HIDE_THREADS), 0, st, B);
 }
 void launch_lmr_side(const Batch& B, cudaStream_t st) {
   if (B.total_chunks == 0) return;

@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(64) k_pass1(Batch B) {
       const uint64_t valid = len >= 64 ? ~0ull : ((1ull << len) - 1ull);
       zrow = (uint32_t)__popcll(~lb & valid);
     }
+    // per tile row, for the fused decode's split strips (written whatever the split, so
+    // that a plan may change its split between runs of the later stages)
+    if (B.count_rows) B.rowcnt[(size_t)g * TILE + r] = (uint8_t)zrow;
     zrow = __reduce_add_sync(0xffffffffu, zrow);
     if (lane == 0) zero_cnt[warp][0] = zrow;
     if (len < 64) auxbits &= len > 0 ? ((len == 64) ? ~0ull : ((1ull << len) - 1)) : 0ull;

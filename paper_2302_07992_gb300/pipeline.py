@@ -107,6 +107,12 @@ class BatchedPipeline:
         for pl, op in self.plans:
             pl.run(op, stream)
 
+    def plan(self, op):
+        return next(pl for pl, o in self.plans if o == op)
+
+    def jobs(self, op):
+        return [self.s.job(op, i) for i in range(self.s.n)]
+
     def capture(self):
         """Record one step into a CUDA graph (plans issue memsets and kernels only)."""
         side = torch.cuda.Stream()

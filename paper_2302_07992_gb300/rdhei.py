@@ -81,6 +81,11 @@ _lib.rdhei_plan_stage_active.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c
 _lib.rdhei_plan_stage_active.restype = ctypes.c_int
 _lib.rdhei_plan_set_wave_cols.argtypes = [ctypes.c_void_p, ctypes.c_int]
 _lib.rdhei_plan_set_wave_cols.restype = ctypes.c_int
+_lib.rdhei_plan_set_param.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+_lib.rdhei_plan_set_param.restype = ctypes.c_int
+_lib.rdhei_plan_get_param.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.rdhei_plan_get_param.restype = ctypes.c_int
+PARAM_WAVE_COLS, PARAM_EXTRACT_ROWS, PARAM_ENC_SPLIT = 1, 2, 3
 _lib.rdhei_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.rdhei_plan_destroy.restype = None
 _lib.rdhei_workspace_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
@@ -210,13 +215,15 @@ class Plan:
     """A validated, uploaded batch: ``run(op)`` launches kernels only (capturable)."""
 
     def __init__(self, jobs: list[Job], stream=None, workspace: torch.Tensor | None = None,
-                 wave_cols: int | None = None):
+                 wave_cols: int | None = None, params: dict | None = None):
         self._jobs = (Job * len(jobs))(*jobs)
         h = ctypes.c_void_p()
         _check(_lib.rdhei_plan_create(self._jobs, len(jobs), ctypes.byref(h)), "rdhei_plan_create")
         self._h = h
         if wave_cols is not None:
             _check(_lib.rdhei_plan_set_wave_cols(h, int(wave_cols)), "rdhei_plan_set_wave_cols")
+        for k, v in (params or {}).items():
+            self.set_param(k, v)
         self.wave_cols = wave_cols
         need = _lib.rdhei_plan_workspace_size(h)
         if workspace is None or workspace.numel() < need:
@@ -234,6 +241,13 @@ class Plan:
     def run_stage(self, op: int, stage: int, stream=None):
         _check(_lib.rdhei_plan_run_stage(self._h, int(op), int(stage), _stream(stream)),
                f"rdhei_plan_run_stage({op}, {stage})")
+
+    def set_param(self, param: int, value: int):
+        """A free launch parameter (PARAM_*); results do not depend on it."""
+        _check(_lib.rdhei_plan_set_param(self._h, int(param), int(value)), f"rdhei_plan_set_param({param})")
+
+    def get_param(self, param: int) -> int:
+        return int(_lib.rdhei_plan_get_param(self._h, int(param)))
 
     def active_stages(self, op: int) -> list[int]:
         """Stages of op that launch work for this plan's jobs."""
