@@ -228,7 +228,8 @@ int rdhei_plan_set_wave_cols(rdhei_plan *plan, int cols);
 /* Free launch parameters of a plan (the autotuner's knobs; results do not depend on them):
  *   RDHEI_PARAM_EXTRACT_ROWS  rows of a 64-row strip that one rdhei_decode extraction CTA
  *                             handles: 64, 32, 16, 8 or 4; 0 = chosen per batch (whole
- *                             strips unless the batch has fewer than 8 strips per SM).
+ *                             strips, or 16 rows when the batch has fewer than 4 strips
+ *                             per SM).
  *                             Takes effect at the next run.
  *   RDHEI_PARAM_ENC_SPLIT     CTAs that share one tile row of rdhei_label_encrypt's gather:
  *                             1..64; 0 = chosen per batch (more for small batches).  Takes

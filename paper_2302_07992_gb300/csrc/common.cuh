@@ -240,6 +240,10 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Asynchronous global -> shared copies (cp.async): commit and wait for the groups.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void set_error(uint32_t* err, int code) { atomicCAS(err, 0u, (uint32_t)code); }
 
 // Index checks of the checked build (-DRDHEI_CHECK, a stand-in for a memory checker):

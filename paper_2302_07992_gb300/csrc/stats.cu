@@ -244,8 +244,7 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, int bytes)
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                "l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// (cp_async_commit / cp_async_wait_all: common.cuh)
 
 // Stage the (SS_TY + 10) x SS_PITCH input rectangle of both images for one tile.
 // 16-byte or 4-byte asynchronous copies when the rows allow it (zero-filled outside
