@@ -201,6 +201,14 @@ typedef struct rdhei_plan rdhei_plan;
 int rdhei_plan_create(const rdhei_job *jobs, int n, rdhei_plan **plan);
 size_t rdhei_plan_workspace_size(const rdhei_plan *plan);
 int rdhei_plan_upload(rdhei_plan *plan, void *ws, size_t ws_bytes, void *stream);
+/* The same without waiting: the descriptors are written into `staging` (caller-owned
+ * PAGE-LOCKED host memory of at least rdhei_plan_staging_size() bytes) and copied from
+ * there asynchronously on `stream`; the caller keeps `staging` untouched until the
+ * stream has passed the copy (for example until the plan's work on that stream has
+ * completed).  Returns RDHEI_ESPACE for a staging buffer that is too small. */
+size_t rdhei_plan_staging_size(const rdhei_plan *plan);
+int rdhei_plan_upload_async(rdhei_plan *plan, void *ws, size_t ws_bytes, void *staging, size_t staging_bytes,
+                            void *stream);
 int rdhei_plan_run(rdhei_plan *plan, int op, void *stream);
 void rdhei_plan_destroy(rdhei_plan *plan);
 

@@ -264,10 +264,21 @@ int rdhei_plan_create(const rdhei_job* jobs, int n, rdhei_plan** out) {
 
 size_t rdhei_plan_workspace_size(const rdhei_plan* p) { return p ? p->total : 0; }
 
-int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
+size_t rdhei_plan_staging_size(const rdhei_plan* p) {
+  return p ? p->off_strip_owner + (size_t)p->total_strips * 4 - p->off_desc : 0;
+}
+
+// Descriptors, prefixes and owner tables as one host image of the workspace's
+// descriptor region, copied once: from `staging` (caller-owned, page-locked, valid until
+// the stream passes the copy) without waiting, else from a temporary host buffer and
+// waiting for the copy.
+static int upload_impl(rdhei_plan* p, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
+                       void* stream) {
   if (!p || !ws) return RDHEI_EINVAL;
   if (ws_bytes < p->total) return RDHEI_ESPACE;
   if (reinterpret_cast<uintptr_t>(ws) & 255) return RDHEI_EINVAL;
+  const size_t lo = p->off_desc, hi = p->off_strip_owner + (size_t)p->total_strips * 4;
+  if (staging && staging_bytes < hi - lo) return RDHEI_ESPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   uint8_t* base = reinterpret_cast<uint8_t*>(ws);
   const int n = (int)p->jobs.size();
@@ -275,23 +286,27 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
     p->desc[i].stash = base + p->stash_off[i];
     p->desc[i].ebuf = base + p->ebuf_off[i];
   }
-  // one host image of the descriptor region, copied once
-  const size_t lo = p->off_desc, hi = p->off_strip_owner + (size_t)p->total_strips * 4;
-  std::vector<uint8_t> host(hi - lo, 0);
-  if (n) std::memcpy(host.data(), p->desc.data(), (size_t)n * sizeof(ImgDesc));
-  std::memcpy(host.data() + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
-  std::memcpy(host.data() + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
-  std::memcpy(host.data() + (p->off_z2_prefix - lo), p->z2_prefix.data(), (size_t)(n + 1) * 4);
-  std::memcpy(host.data() + (p->off_strip_prefix - lo), p->strip_prefix.data(), (size_t)(n + 1) * 4);
+  std::vector<uint8_t> tmp;
+  uint8_t* host = reinterpret_cast<uint8_t*>(staging);
+  if (!host) {
+    tmp.assign(hi - lo, 0);
+    host = tmp.data();
+  } else {
+    std::memset(host, 0, hi - lo);
+  }
+  if (n) std::memcpy(host, p->desc.data(), (size_t)n * sizeof(ImgDesc));
+  std::memcpy(host + (p->off_tile_prefix - lo), p->tile_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host + (p->off_chunk_prefix - lo), p->chunk_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host + (p->off_z2_prefix - lo), p->z2_prefix.data(), (size_t)(n + 1) * 4);
+  std::memcpy(host + (p->off_strip_prefix - lo), p->strip_prefix.data(), (size_t)(n + 1) * 4);
   if (p->total_wave)
-    std::memcpy(host.data() + (p->off_wave_list - lo), p->wave_list.data(), (size_t)p->total_wave * sizeof(uint2));
+    std::memcpy(host + (p->off_wave_list - lo), p->wave_list.data(), (size_t)p->total_wave * sizeof(uint2));
   if (p->total_tiles)
-    std::memcpy(host.data() + (p->off_tile_owner - lo), p->tile_owner.data(), (size_t)p->total_tiles * 4);
+    std::memcpy(host + (p->off_tile_owner - lo), p->tile_owner.data(), (size_t)p->total_tiles * 4);
   if (p->total_strips)
-    std::memcpy(host.data() + (p->off_strip_owner - lo), p->strip_owner.data(), (size_t)p->total_strips * 4);
-  if (cudaMemcpyAsync(base + lo, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return RDHEI_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // host buffer is released next
+    std::memcpy(host + (p->off_strip_owner - lo), p->strip_owner.data(), (size_t)p->total_strips * 4);
+  if (cudaMemcpyAsync(base + lo, host, hi - lo, cudaMemcpyHostToDevice, st) != cudaSuccess) return RDHEI_ECUDA;
+  if (!staging && cudaStreamSynchronize(st) != cudaSuccess) return RDHEI_ECUDA;   // tmp is released next
   p->ws = ws;
   Batch& B = p->batch;
   B.desc = reinterpret_cast<const ImgDesc*>(base + p->off_desc);
@@ -329,6 +344,16 @@ int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
   B.part_rows = TILE;
   B.count_rows = 0;
   return RDHEI_OK;
+}
+
+int rdhei_plan_upload(rdhei_plan* p, void* ws, size_t ws_bytes, void* stream) {
+  return upload_impl(p, ws, ws_bytes, nullptr, 0, stream);
+}
+
+int rdhei_plan_upload_async(rdhei_plan* p, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
+                            void* stream) {
+  if (!staging) return RDHEI_EINVAL;
+  return upload_impl(p, ws, ws_bytes, staging, staging_bytes, stream);
 }
 
 static bool aligned4(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 3) == 0; }

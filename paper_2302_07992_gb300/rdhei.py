@@ -69,6 +69,11 @@ _lib.rdhei_plan_workspace_size.argtypes = [ctypes.c_void_p]
 _lib.rdhei_plan_workspace_size.restype = ctypes.c_size_t
 _lib.rdhei_plan_upload.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
 _lib.rdhei_plan_upload.restype = ctypes.c_int
+_lib.rdhei_plan_staging_size.argtypes = [ctypes.c_void_p]
+_lib.rdhei_plan_staging_size.restype = ctypes.c_size_t
+_lib.rdhei_plan_upload_async.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p]
+_lib.rdhei_plan_upload_async.restype = ctypes.c_int
 _lib.rdhei_plan_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
 _lib.rdhei_plan_run.restype = ctypes.c_int
 _lib.rdhei_plan_run_stage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
@@ -215,7 +220,10 @@ class Plan:
     """A validated, uploaded batch: ``run(op)`` launches kernels only (capturable)."""
 
     def __init__(self, jobs: list[Job], stream=None, workspace: torch.Tensor | None = None,
-                 wave_cols: int | None = None, params: dict | None = None):
+                 wave_cols: int | None = None, params: dict | None = None, staging=None):
+        """staging: a callable nbytes -> page-locked uint8 host tensor; when given, the
+        descriptors go up asynchronously from it (rdhei_plan_upload_async) and the
+        caller keeps self.staging alive until the stream has passed the upload."""
         self._jobs = (Job * len(jobs))(*jobs)
         h = ctypes.c_void_p()
         _check(_lib.rdhei_plan_create(self._jobs, len(jobs), ctypes.byref(h)), "rdhei_plan_create")
@@ -232,8 +240,16 @@ class Plan:
         off = (-self.ws.data_ptr()) % 256
         self._ws_ptr = self.ws.data_ptr() + off
         self._ws_bytes = self.ws.numel() - off
-        _check(_lib.rdhei_plan_upload(h, ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _stream(stream)),
-               "rdhei_plan_upload")
+        self.staging = None
+        if staging is None:
+            _check(_lib.rdhei_plan_upload(h, ctypes.c_void_p(self._ws_ptr), self._ws_bytes, _stream(stream)),
+                   "rdhei_plan_upload")
+        else:
+            nb = int(_lib.rdhei_plan_staging_size(h))
+            self.staging = staging(max(nb, 16))
+            _check(_lib.rdhei_plan_upload_async(h, ctypes.c_void_p(self._ws_ptr), self._ws_bytes,
+                                                ctypes.c_void_p(self.staging.data_ptr()), self.staging.numel(),
+                                                _stream(stream)), "rdhei_plan_upload_async")
 
     def run(self, op: int, stream=None):
         _check(_lib.rdhei_plan_run(self._h, int(op), _stream(stream)), f"rdhei_plan_run({op})")

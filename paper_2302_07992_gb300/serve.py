@@ -1,9 +1,10 @@
 """Continuous-batching request loop for encode and decode requests on one GPU.
 
-  encode request: an original image and a message -> rdhei_label_encrypt + rdhei_embed
+  encode request: an original image and a message -> rdhei_encode (owner + hider)
                   -> marked image (and, for LMR, the rotated maps);
-  decode request: a marked image (+ LMR maps) -> rdhei_extract + rdhei_decrypt_recover
+  decode request: a marked image (+ LMR maps) -> rdhei_decode (receiver with both keys)
                   -> message bits and recovered image.
+(CudaExecutor(fused=False) runs the four separable calls instead.)
 
 Device-resident state: an encode request with keep_state leaves its rotated LMR maps
 (map l and first-MSB map eta, 2 bits a pixel) in device memory and returns a handle; a
@@ -13,8 +14,9 @@ least recently used entries beyond its own cap.
 
 Admission, batching, cancellation, failure handling and metrics are the device-free
 scheduler of ``sched``; this module supplies its CUDA executor.  Each admitted group
-of same-kind requests becomes one batch: one plan per operation over all its images,
-launched on its own stream, with host<->device copies on that stream.  New batches
+of same-kind requests becomes one batch: one plan over all its images, its descriptors
+uploaded asynchronously from a pinned staging buffer, launched on its own stream, with
+host<->device copies on that stream -- nothing in a launch waits for the device.  New batches
 are formed and launched while earlier ones run, so work of requests that arrive while
 others are on the GPU overlaps on the device.  A request's latency is arrival -> its
 batch's completion (results back in host memory).  All work is in the library's
@@ -104,7 +106,8 @@ class CudaExecutor:
     operation, pinned result buffers from a PinnedPool."""
 
     def __init__(self, streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None,
-                 state: "DeviceState | None" = None):
+                 state: "DeviceState | None" = None, fused: bool = True):
+        self.fused = fused
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
         self.free_streams = deque(self.streams)
@@ -176,9 +179,16 @@ class CudaExecutor:
             self.state.drop(result["state"])
 
     def release(self, bt: _Batch):
+        for pl in bt.plans:
+            if getattr(pl, "staging", None) is not None:
+                self.pool.give(pl.staging)          # the upload is long done: the batch completed
+                pl.staging = None
         bt.keep.clear()
         bt.plans.clear()
         self.free_streams.append(bt.stream)
+
+    def _plan(self, jobs, st):
+        return rd.Plan(jobs, st, staging=lambda nb: self.pool.take((nb,)))
 
     def _arena(self, sizes, zero: bool, dev):
         """One device allocation cut into 256-byte-aligned pieces of the given sizes
@@ -196,14 +206,14 @@ class CudaExecutor:
         return max(4, ((int(nbits) + 31) // 32) * 4)
 
     def _launch_encode(self, bt, reqs, st, dev):
-        # buffers and plans first (a plan upload waits for its stream), then copies and work
+        # buffers and plans first, then copies and work, all on the batch's stream
         n = len(reqs)
         px = [r.pixels for r in reqs]
         lmr = [(r.params.variant & 1) == rd.LMR for r in reqs]
-        img_arena, views = self._arena(px * 3, False, dev)
+        img_arena, views = self._arena(px * (2 if self.fused else 3), False, dev)
         imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
-        enc = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
-        marked = [v.view(*r.image.shape) for v, r in zip(views[2 * n:], reqs)]
+        marked = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
+        enc = [v.view(*r.image.shape) for v, r in zip(views[2 * n:], reqs)]     # separable calls only
         keep = [l and r.keep_state for l, r in zip(lmr, reqs)]
         bit_arena, bviews = self._arena([self._words(p) if l and not k else None for p, l, k in zip(px, lmr, keep)]
                                         * 2 + [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
@@ -217,16 +227,22 @@ class CudaExecutor:
                 buf = torch.empty(2 * w, dtype=torch.uint8, device=dev)
                 maps[i], etas[i] = buf[:w], buf[w:]
                 kept[i] = buf
-        j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=enc[i], map_bits=maps[i], eta_bits=etas[i],
-                          info=info[i]) for i, r in enumerate(reqs)]
-        j2 = [rd.make_job(r.params, *r.image.shape, src=enc[i], dst=marked[i], map_bits=maps[i], payload=pays[i],
-                          nbits=r.nbits, info=info[i], b=0) for i, r in enumerate(reqs)]
-        p1, p2 = rd.Plan(j1, st), rd.Plan(j2, st)
+        if self.fused:
+            jf = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=marked[i], map_bits=maps[i],
+                              eta_bits=etas[i], payload=pays[i], nbits=r.nbits, info=info[i])
+                  for i, r in enumerate(reqs)]
+            plans = [(self._plan(jf, st), rd.OP_ENCODE)]
+        else:
+            j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=enc[i], map_bits=maps[i],
+                              eta_bits=etas[i], info=info[i]) for i, r in enumerate(reqs)]
+            j2 = [rd.make_job(r.params, *r.image.shape, src=enc[i], dst=marked[i], map_bits=maps[i],
+                              payload=pays[i], nbits=r.nbits, info=info[i], b=0) for i, r in enumerate(reqs)]
+            plans = [(self._plan(j1, st), rd.OP_LABEL_ENCRYPT), (self._plan(j2, st), rd.OP_EMBED)]
         for i, r in enumerate(reqs):
             imgs[i].copy_(r.image, non_blocking=True)
             pays[i][: r.payload.numel()].copy_(r.payload, non_blocking=True)
-        p1.run(rd.OP_LABEL_ENCRYPT, st)
-        p2.run(rd.OP_EMBED, st)
+        for pl, op in plans:
+            pl.run(op, st)
         outs = []
         for i, r in enumerate(reqs):
             h = self.pool.take(tuple(r.image.shape))
@@ -243,9 +259,9 @@ class CudaExecutor:
             outs.append(o)
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
-        bt.hcodes = self._error_words(p1, p2)
+        bt.hcodes = self._error_words(*[pl for pl, _ in plans])
         bt.keep += [img_arena, bit_arena]
-        bt.plans = [p1, p2]
+        bt.plans = [pl for pl, _ in plans]
         bt.outs, bt.hinfo = outs, hinfo
 
     def _launch_decode(self, bt, reqs, st, dev):
@@ -271,18 +287,23 @@ class CudaExecutor:
                 bt.keep.append(h)                   # alive until the batch completes, even if evicted
         bit_arena, bviews = self._arena([self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
         bits, info = bviews[:n], bviews[-1].view(n, rd.INFO_BYTES)
-        j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], map_bits=maps[i], bits_out=bits[i], max_bits=r.nbits,
-                          info=info[i], b=r.b) for i, r in enumerate(reqs)]
-        j2 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=rec[i], map_bits=maps[i], eta_bits=etas[i],
-                          info=info[i], b=r.b) for i, r in enumerate(reqs)]
-        p1, p2 = rd.Plan(j1, st), rd.Plan(j2, st)
+        if self.fused:
+            jf = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=rec[i], map_bits=maps[i], eta_bits=etas[i],
+                              bits_out=bits[i], max_bits=r.nbits, info=info[i], b=r.b) for i, r in enumerate(reqs)]
+            plans = [(self._plan(jf, st), rd.OP_DECODE)]
+        else:
+            j1 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], map_bits=maps[i], bits_out=bits[i],
+                              max_bits=r.nbits, info=info[i], b=r.b) for i, r in enumerate(reqs)]
+            j2 = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=rec[i], map_bits=maps[i],
+                              eta_bits=etas[i], info=info[i], b=r.b) for i, r in enumerate(reqs)]
+            plans = [(self._plan(j1, st), rd.OP_EXTRACT), (self._plan(j2, st), rd.OP_DECRYPT_RECOVER)]
         for i, r in enumerate(reqs):
             imgs[i].copy_(r.image, non_blocking=True)
             if maps[i] is not None and held[i] is None:
                 maps[i].copy_(r.lmr_map.reshape(-1), non_blocking=True)
                 etas[i].copy_(r.lmr_eta.reshape(-1), non_blocking=True)
-        p1.run(rd.OP_EXTRACT, st)
-        p2.run(rd.OP_DECRYPT_RECOVER, st)
+        for pl, op in plans:
+            pl.run(op, st)
         outs = []
         for i, r in enumerate(reqs):
             hb = self.pool.take(tuple(bits[i].shape))
@@ -292,9 +313,9 @@ class CudaExecutor:
             outs.append({"bits": hb, "recovered": hr})
         hinfo = self.pool.take(tuple(info.shape))
         hinfo.copy_(info, non_blocking=True)
-        bt.hcodes = self._error_words(p1, p2)
+        bt.hcodes = self._error_words(*[pl for pl, _ in plans])
         bt.keep += [img_arena, bit_arena]
-        bt.plans = [p1, p2]
+        bt.plans = [pl for pl, _ in plans]
         bt.outs, bt.hinfo = outs, hinfo
 
 
@@ -303,8 +324,9 @@ class Server(Scheduler):
 
     def __init__(self, budget_bytes: float = 40e9, max_batch: int = 64, max_batch_pixels: int = 1 << 27,
                  streams: int = 4, device: int = 0, pool: "PinnedPool | None" = None,
-                 max_queue: int | None = None, state: "DeviceState | None" = None, admit_window_ms: float = 0.0):
-        ex = CudaExecutor(streams, device, pool, state)
+                 max_queue: int | None = None, state: "DeviceState | None" = None, admit_window_ms: float = 0.0,
+                 fused: bool = True):
+        ex = CudaExecutor(streams, device, pool, state, fused)
         super().__init__(ex, budget_bytes, max_batch, max_batch_pixels, max_queue, admit_window_ms=admit_window_ms)
         self.pool = ex.pool
         self.state = ex.state

@@ -211,3 +211,56 @@ def test_fused_rejects_missing_buffers(rd):
     j = rd.make_job(p, 64, 64, src=img, map_bits=rd.bitbuf(4096), eta_bits=rd.bitbuf(4096), info=info)
     with pytest.raises(rd.RdheiError):
         rd.run_jobs(rd.OP_DECODE, [j])
+
+
+def test_async_upload_on_a_side_stream(rd):
+    """Plans whose descriptors go up from a pinned staging buffer (rdhei_plan_upload_async),
+    created and run on a non-default stream with no synchronisation in between, give the
+    bytes of plans uploaded synchronously; a staging buffer that is missing or too small
+    is refused before anything is queued."""
+    shapes = [(300, 470), (64, 4096), (129, 130)]
+    variants = [oracle.EMR, oracle.LMR, oracle.LMR_MED]
+    n = len(shapes)
+    imgs = [torch.from_numpy(synth.synth_image(h, w, 900 + i)).cuda() for i, (h, w) in enumerate(shapes)]
+    P = [_params(rd, variants[i], 910 + i)[0] for i in range(n)]
+    lmr = [(v & 1) == rd.LMR for v in variants]
+    caps = [im.numel() for im in imgs]          # payload longer than any capacity: embedding stops there
+    pays = [rd.as_bitbuf(torch.from_numpy(synth.payload_bits(920 + i, caps[i])), caps[i]) for i in range(n)]
+
+    def run(staged, stream):
+        info = rd.new_info(n)
+        marked = [torch.empty_like(x) for x in imgs]
+        maps = [rd.bitbuf(x.numel()) for x in imgs]
+        etas = [rd.bitbuf(x.numel()) if lmr[i] else None for i, x in enumerate(imgs)]
+        bits = [rd.bitbuf(caps[i]) for i in range(n)]
+        rec = [torch.empty_like(x) for x in imgs]
+        stage = (lambda nb: torch.empty(nb, dtype=torch.uint8, pin_memory=True)) if staged else None
+        with torch.cuda.stream(stream):
+            pe = rd.Plan([rd.make_job(P[i], *shapes[i], src=imgs[i], dst=marked[i], map_bits=maps[i],
+                                      eta_bits=etas[i], payload=pays[i], nbits=caps[i], info=info[i])
+                          for i in range(n)], stream, staging=stage)
+            pe.run(rd.OP_ENCODE, stream)
+            pd = rd.Plan([rd.make_job(P[i], *shapes[i], src=marked[i], dst=rec[i],
+                                      map_bits=maps[i] if lmr[i] else None, eta_bits=etas[i], bits_out=bits[i],
+                                      max_bits=caps[i], info=info[i], b=0) for i in range(n)], stream, staging=stage)
+            pd.run(rd.OP_DECODE, stream)
+        stream.synchronize()
+        assert pe.status() in (0, rd.RDHEI_ECAPACITY) and pd.status() == 0
+        return [t.cpu() for t in marked + bits + rec], rd.read_info(info)
+
+    torch.cuda.synchronize()
+    ref, iref = run(False, torch.cuda.current_stream())
+    got, igot = run(True, torch.cuda.Stream())
+    assert iref == igot
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+
+    plan = rd.Plan([rd.make_job(P[0], *shapes[0], src=imgs[0], dst=torch.empty_like(imgs[0]), info=rd.new_info(1))])
+    need = int(rd._lib.rdhei_plan_staging_size(plan._h))
+    small = torch.empty(max(need - 16, 16), dtype=torch.uint8, pin_memory=True)
+    import ctypes
+    rc = rd._lib.rdhei_plan_upload_async(plan._h, ctypes.c_void_p(plan._ws_ptr), plan._ws_bytes,
+                                         ctypes.c_void_p(small.data_ptr()), small.numel(), None)
+    assert rc == rd.RDHEI_ESPACE
+    rc = rd._lib.rdhei_plan_upload_async(plan._h, ctypes.c_void_p(plan._ws_ptr), plan._ws_bytes, None, 0, None)
+    assert rc == rd.RDHEI_EINVAL
