@@ -104,6 +104,17 @@ def test_fused_partial_payload_and_limits(rd, frac, max_frac):
     _fused(rd, img, oracle.LMR, 30, frac=frac, max_frac=max_frac)
 
 
+@pytest.mark.parametrize("shape,frac", [((150, 1040), 1.0), ((150, 1040), 0.41), ((64, 2048), 0.2),
+                                        ((64, 2048), 1.0), ((97, 528), 0.77), ((70, 16), 1.0)])
+def test_fused_wide_rows_and_short_messages(rd, shape, frac):
+    """Rows of several 512-pixel spans, strips whose message ends mid-row or overflows
+    one staged window of K2 words, and an image narrower than a 16-pixel load."""
+    H, W = shape
+    img = synth.synth_image(H, W, H + W)
+    _fused(rd, img, oracle.EMR, 40 + H, frac=frac)
+    _fused(rd, img, oracle.LMR, 41 + H, frac=frac)
+
+
 def test_fused_edge_images(rd):
     # constant (every non-first pixel redundant, b = 7), no redundancy at all (no slots),
     # and an image whose top half has no slots (whole strips with empty slot ranges)
