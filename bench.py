@@ -343,6 +343,13 @@ def run_gpu(args, rank, world, local_rank):
                                          max_bits=caps[k], info=info[k], b=0))
         plans = [(rd.Plan(fenc_jobs, stream), rd.OP_ENCODE),
                  (rd.Plan(fdec_jobs, stream, wave_cols=wave_cols), rd.OP_DECODE)]
+        # the extraction's rows per CTA from the autotuner (cached per device and batch
+        # shape), timed on the marked images of one untimed encode
+        from paper_2302_07992_gb300 import tune
+        plans[0][0].run(rd.OP_ENCODE, stream)
+        rows, times = tune.best_extract_rows(fdec_jobs, stream)
+        plans[1][0].set_param(rd.PARAM_EXTRACT_ROWS, rows)
+        tuning = dict(tuning or {}, extract_rows=rows, ms_per_extract_rows=times)
     else:
         plan_emb, plan_ext = rd.Plan(emb_jobs, stream), rd.Plan(ext_jobs, stream)
         plan_dec = rd.Plan(dec_jobs, stream, wave_cols=wave_cols)
