@@ -344,9 +344,12 @@ def run_gpu(args, rank, world, local_rank):
         plans = [(rd.Plan(fenc_jobs, stream), rd.OP_ENCODE),
                  (rd.Plan(fdec_jobs, stream, wave_cols=wave_cols), rd.OP_DECODE)]
         # the extraction's rows per CTA from the autotuner (cached per device and batch
-        # shape), timed on the marked images of one untimed encode
+        # shape), timed on the marked images of one untimed encode.  One untimed decode
+        # runs whether or not the tuner has a cached value, so the kernels launch in the
+        # same order either way (the ncu captures select launches by position).
         from paper_2302_07992_gb300 import tune
         plans[0][0].run(rd.OP_ENCODE, stream)
+        plans[1][0].run(rd.OP_DECODE, stream)
         rows, times = tune.best_extract_rows(fdec_jobs, stream)
         plans[1][0].set_param(rd.PARAM_EXTRACT_ROWS, rows)
         tuning = dict(tuning or {}, extract_rows=rows, ms_per_extract_rows=times)
