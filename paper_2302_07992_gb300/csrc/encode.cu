@@ -229,7 +229,8 @@ struct EncSmem {
 struct NoPre {
   __device__ __forceinline__ void operator()() const {}
 };
-template <bool ANY_LMR, bool ANY_MED, typename Pre = NoPre>
+// SKEW: the source tile and label plane in the chunk-skewed layout (skewed_chunk).
+template <bool ANY_LMR, bool ANY_MED, bool SKEW = false, typename Pre = NoPre>
 __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, uint32_t nsplit, uint32_t piece,
                                               EncSmem<ANY_LMR, ANY_MED>& sm, const Pre& pre = Pre()) {
   uint8_t* const tin = sm.tin;
@@ -255,7 +256,7 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
   const uint32_t per = (tiles_x + nsplit - 1) / nsplit;
   const uint32_t tx0 = piece * per, tx1 = min(tx0 + per, tiles_x);
   if (tx0 >= tx1) return;
-  const int row = t >> 2, quarter = t & 3;
+  const int row = tile_row_of(t), quarter = t & 3;
   if (t < 16) selt[t] = pair_selectors(t & 3u, t >> 2);
 
   // source tile of output tile (qty, tx): its angle sum above level 6, my 16 bytes of
@@ -320,7 +321,7 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
     const int py0 = (int)(P / tiles_x) * TILE, px0 = (int)(P % tiles_x) * TILE;
 
     // 1. P, its halo column and its subtree into shared memory
-    *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(skewed_chunk<SKEW>(tin, row, quarter)) = make_uint4(w[0], w[1], w[2], w[3]);
     if (quarter == 0) halo[row] = (uint8_t)nhalo;
     if (t < SUBTREE_BYTES / 4) reinterpret_cast<uint32_t*>(sub)[t] = nsub;
     if (ANY_MED && med && row == 0) {
@@ -333,7 +334,7 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
     // 2. location map with this image's b: l = 1 where the top b bits differ from the
     //    left neighbour's (first image column: always 1)
     {
-      uint32_t left = quarter == 0 ? (uint32_t)halo[row] : (uint32_t)tin[row * TPITCH + 16 * quarter - 1];
+      uint32_t left = quarter == 0 ? (uint32_t)halo[row] : (uint32_t)skewed_chunk<SKEW>(tin, row, quarter - 1)[15];
       const uint32_t K = (0x80u - (0x100u >> b)) * 0x01010101u;
       uint32_t lw[4];
       if (!med) {
@@ -347,8 +348,9 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
         // related-work MED prediction from the left, upper and upper-left pixels
         const int y = py0 + row, x = px0 + 16 * quarter;
         const bool seven = d.variant == RDHEI_EMR;
-        const uint8_t* ur = row > 0 ? tin + (row - 1) * TPITCH + 16 * quarter : uprow + 16 * quarter;
-        uint32_t ul = quarter > 0 ? ur[-1] : row > 0 ? halo[row - 1] : uprow[TILE];
+        const uint8_t* ur = row > 0 ? skewed_chunk<SKEW>(tin, row - 1, quarter) : uprow + 16 * quarter;
+        uint32_t ul = quarter > 0 ? (row > 0 ? skewed_chunk<SKEW>(tin, row - 1, quarter - 1)[15] : ur[-1])
+                                  : row > 0 ? halo[row - 1] : uprow[TILE];
         if (px0 == 0 && quarter == 0) left = 0;
         const uint4 u4 = *reinterpret_cast<const uint4*>(ur);
         const uint32_t up[4] = {u4.x, u4.y, u4.z, u4.w};
@@ -368,9 +370,9 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
       }
       __syncthreads();   // every thread has read its left byte
       if (LMR) {
-        *reinterpret_cast<uint4*>(lin + row * TPITCH + 16 * quarter) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        *reinterpret_cast<uint4*>(skewed_chunk<SKEW>(lin, row, quarter)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       } else {
-        *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) =
+        *reinterpret_cast<uint4*>(skewed_chunk<SKEW>(tin, row, quarter)) =
             make_uint4((w[0] & 0xFEFEFEFEu) | lw[0], (w[1] & 0xFEFEFEFEu) | lw[1],
                        (w[2] & 0xFEFEFEFEu) | lw[2], (w[3] & 0xFEFEFEFEu) | lw[3]);
       }
@@ -385,12 +387,12 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
       const uint32_t nib = sub_level1_nibbles(sub, pr, pc);
       const uint32_t sT = selt[nib & 0xF], sB = selt[nib >> 4];
       uint32_t w0, w1, w2, w3;
-      ld_micro(tin, pr, pc, w0, w1, w2, w3);
+      ld_micro_skewed<SKEW>(tin, pr, pc, w0, w1, w2, w3);
       turn_subblocks(w0, w1, w2, w3, sT, sB);
       turn4x4(w0, w1, w2, w3, S1);
       st_micro(tout, mr, mc, w0, w1, w2, w3);
       if (LMR) {
-        ld_micro(lin, pr, pc, w0, w1, w2, w3);
+        ld_micro_skewed<SKEW>(lin, pr, pc, w0, w1, w2, w3);
         turn_subblocks(w0, w1, w2, w3, sT, sB);
         turn4x4(w0, w1, w2, w3, S1);
         st_micro(lout, mr, mc, w0, w1, w2, w3);
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(256, 5) k_enc_fused(Batch B) {
   __shared__ EncSmem<ANY_LMR, ANY_MED> sm;
   __shared__ EmbedSmem em;
   const uint32_t s = blockIdx.x;
-  enc_rows_body<ANY_LMR, ANY_MED>(B, s, 1, 0, sm, [&]() { stage_strip(B, s, em); });
+  enc_rows_body<ANY_LMR, ANY_MED, true>(B, s, 1, 0, sm, [&]() { stage_strip(B, s, em); });
   __syncthreads();   // the strip's encrypted pixels (and LMR map bits) are in global memory
   embed_strip(B, s, em);
 }
