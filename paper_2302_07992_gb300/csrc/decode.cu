@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   // the replaced field: EMR top b bits, LMR bits 6 .. 8-b (Sec. III-B-2)
   const uint32_t FM = lmr ? (((1u << (b - 1)) - 1u) << (8 - b)) : ((0xFFu << (8 - b)) & 0xFFu);
   const uint32_t FM4 = FM * 0x01010101u;
-  const int row = t >> 2, quarter = t & 3;
+  const int row = tile_row_of(t), quarter = t & 3;
   const int y = (int)ty * TILE + row;
   if (t < 16) selt[t] = pair_selectors((4u - (t & 3u)) & 3u, (4u - (t >> 2)) & 3u);   // inverse 2x2 turns
 
@@ -77,12 +77,12 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
     const uint32_t P = ty * tiles_x + tx;
     const uint32_t U = nU;
     // 1. the fetched tile and its aux plane into shared memory, the subtree of P
-    *reinterpret_cast<uint4*>(tin + row * TPITCH + 16 * quarter) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+    *reinterpret_cast<uint4*>(skewed_chunk<true>(tin, row, quarter)) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
     {
       uint32_t e[4];
 #pragma unroll
       for (int i = 0; i < 4; i++) e[i] = (((na >> (4 * i)) & 0xFu) * 0x00204081u) & 0x01010101u;
-      *reinterpret_cast<uint4*>(ain + row * TPITCH + 16 * quarter) = make_uint4(e[0], e[1], e[2], e[3]);
+      *reinterpret_cast<uint4*>(skewed_chunk<true>(ain, row, quarter)) = make_uint4(e[0], e[1], e[2], e[3]);
     }
     if (t < SUBTREE_BYTES / 4)
       reinterpret_cast<uint32_t*>(sub)[t] =
@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
       const uint32_t sT = selt[nib & 0xF], sB = selt[nib >> 4];
       const uint32_t inv = (4u - S1) & 3u;
       uint32_t w0, w1, w2, w3;
-      ld_micro(tin, qr, qc, w0, w1, w2, w3);
+      ld_micro_skewed<true>(tin, qr, qc, w0, w1, w2, w3);
       turn4x4(w0, w1, w2, w3, inv);
       turn_subblocks(w0, w1, w2, w3, sT, sB);
       st_micro(tout, mr, mc, w0, w1, w2, w3);
-      ld_micro(ain, qr, qc, w0, w1, w2, w3);
+      ld_micro_skewed<true>(ain, qr, qc, w0, w1, w2, w3);
       turn4x4(w0, w1, w2, w3, inv);
       turn_subblocks(w0, w1, w2, w3, sT, sB);
       st_micro(aout, mr, mc, w0, w1, w2, w3);

@@ -20,9 +20,9 @@ constexpr int TPITCH = 80;   // shared-memory row pitch of a 64-byte tile row (b
 // quarters are four consecutive lanes).  A warp's 16-byte shared accesses of tile rows
 // run in four phases of eight lanes, and with the 80-byte pitch two adjacent rows share
 // four of their sixteen banks; so the lanes of a phase take rows r and r + 4 (80 words
-// apart, disjoint banks) instead of r and r + 1.  Measured: the owner's gather 0.252 ->
-// 0.241 ms on 1000 x 512^2.  The decode gather keeps rows r, r + 1 per phase (t >> 2):
-// there the same mapping measured slower (0.257 -> 0.266 ms).
+// apart, disjoint banks) instead of r and r + 1.  Measured on 1000 x 512^2: the owner's
+// gather 0.252 -> 0.241 ms; the decode gather 0.258 -> 0.254 ms together with the chunk
+// skew below (alone it measured slower there, 0.266 ms).
 __device__ __forceinline__ int tile_row_of(int t) {
   const int lane = t & 31;
   return 8 * (t >> 5) + ((lane >> 3) & 3) + 4 * ((lane >> 2) & 1);
