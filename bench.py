@@ -1228,7 +1228,7 @@ def main():
                          "c4: decode-only 64 x 4096^2; c5: serving latency; stats: security statistics of the c2 batch; lmr_blocks: LMR with "
                          "side information, rotation block-size sweep")
     ap.add_argument("--c5-rate", type=float, default=2000.0)
-    ap.add_argument("--c5-seconds", type=float, default=5.0)
+    ap.add_argument("--c5-seconds", type=float, default=10.0)
     ap.add_argument("--c5-pool", type=int, default=64)
     ap.add_argument("--c5-window-ms", type=float, default=0.5,
                     help="serving: while a batch is on the device, hold arrivals up to this long to batch them")

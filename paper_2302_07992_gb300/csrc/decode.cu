@@ -13,6 +13,18 @@
 
 namespace rdhei {
 
+// Byte-permute selector for a word whose label-1 bytes form the pattern z (bit k = byte
+// k): result byte j takes byte j' of the word, j' the last label-1 byte at or before j,
+// or byte 4 (the carried field) when bytes 0..j are all label 0.
+__host__ __device__ __forceinline__ uint32_t fill_selector(uint32_t z) {
+  uint32_t sel = 0, src = 4;
+  for (int j = 0; j < 4; j++) {
+    if ((z >> j) & 1u) src = (uint32_t)j;
+    sel |= src << (4 * j);
+  }
+  return sel;
+}
+
 template <bool ANY_LMR, bool ANY_MED>
 __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
@@ -24,6 +36,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   __shared__ __align__(16) uint8_t sub[SUBTREE_BYTES];
   __shared__ uint32_t selt[16];
   __shared__ uint8_t rowcarry[TILE];
+  __shared__ uint32_t fillsel[16];
 
   const int t = threadIdx.x;
   const uint32_t s = blockIdx.x;
@@ -42,6 +55,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
   const int row = tile_row_of(t), quarter = t & 3;
   const int y = (int)ty * TILE + row;
   if (t < 16) selt[t] = pair_selectors((4u - (t & 3u)) & 3u, (4u - (t >> 2)) & 3u);   // inverse 2x2 turns
+  if (t >= 16 && t < 32) fillsel[t - 16] = fill_selector(t - 16);
 
   // rotated tile of original tile (ty, tx): my 16 bytes of the stash and 16 aux bits
   uint32_t nw[4], na = 0, nU = 0;
@@ -110,18 +124,15 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
     }
     __syncthreads();
 
-    // 3. labels and decrypted values; inside my 16 pixels every label-0 pixel takes the
-    //    field of the last label-1 pixel to its left (log-step over the bytes of a word,
-    //    then word to word)
+    // 3. labels and decrypted values of my 16 pixels
     const int x = (int)tx * TILE + 16 * quarter;
     int valid = (y < H) ? min(16, W - x) : 0;
     if (valid < 0) valid = 0;
-    uint32_t v[4], xf[4], mm[4], labs[4];
+    uint32_t v[4], lw[4];
     {
       const uint4 v4 = *reinterpret_cast<const uint4*>(tout + row * TPITCH + 16 * quarter);
       const uint4 a4 = *reinterpret_cast<const uint4*>(aout + row * TPITCH + 16 * quarter);
       const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w}, aa[4] = {a4.x, a4.y, a4.z, a4.w};
-      uint32_t lw[4];
 #pragma unroll
       for (int i = 0; i < 4; i++) {
         if (lmr) {
@@ -140,20 +151,6 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
         }
       }
       if (x == 0 && valid > 0 && !med) lw[0] |= 1u;              // first image column: non-redundant
-      uint32_t carry = 0, carried = 0;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const uint32_t lab = lw[i];
-        if (ANY_MED) labs[i] = lab;
-        uint32_t m = lab * 0xFFu;
-        uint32_t f = v[i] & FM4 & m;
-        f |= ~m & (f << 8);  m |= m << 8;
-        f |= ~m & (f << 16); m |= m << 16;
-        f |= ~m & carry;     m |= carried;
-        xf[i] = f; mm[i] = m;
-        carry = (f >> 24) * 0x01010101u;
-        carried = (uint32_t)((int32_t)m >> 31);
-      }
     }
     if (ANY_MED && med) {
       // MED variant: the prediction needs recovered upper neighbours, so this pass only
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
       // restores the fields
       uint32_t bits16 = 0;
 #pragma unroll
-      for (int i = 0; i < 4; i++) bits16 |= ((((labs[i] & 0x01010101u) * 0x01020408u) >> 24) & 0xFu) << (4 * i);
+      for (int i = 0; i < 4; i++) bits16 |= ((((lw[i] & 0x01010101u) * 0x01020408u) >> 24) & 0xFu) << (4 * i);
       reinterpret_cast<uint16_t*>(B.lab + (size_t)(d.tile_base + P) * AUX_BYTES)[row * 4 + quarter] = (uint16_t)bits16;
       if (valid > 0) {
         uint8_t* dst = d.dst + (size_t)y * W + x;
@@ -176,9 +173,21 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
       __syncthreads();
       continue;
     }
-    // 4. carry into my 16 pixels: the last label-1 field of the quarters to my left,
-    //    else the strip's carry from the previous tile
-    const uint32_t has = mm[3] >> 31, fld = (xf[3] >> 24) & FM;
+    // 4. the field of the last label-1 pixel among my 16, then the carry into them: the
+    //    last such field of the quarters to my left, else the strip's carry from the
+    //    previous tile
+    uint32_t zw[4];                                               // label pattern per word, bit k = byte k
+#pragma unroll
+    for (int i = 0; i < 4; i++) zw[i] = (lw[i] * 0x01020408u) >> 24;
+    const uint32_t pat = zw[0] | (zw[1] << 4) | (zw[2] << 8) | (zw[3] << 12);
+    const uint32_t has = pat != 0u;
+    uint32_t fld = 0;
+    {
+      const uint32_t lb = 31u - (uint32_t)__clz(pat | 1u);       // last label-1 byte (when has)
+      const uint32_t w01 = (lb & 4u) ? v[1] : v[0], w23 = (lb & 4u) ? v[3] : v[2];
+      const uint32_t w = (lb & 8u) ? w23 : w01;
+      if (has) fld = (w >> (8u * (lb & 3u))) & FM;
+    }
     uint32_t ch = has, cf = fld;   // inclusive scan across the row's 4 lanes, "last one wins"
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {
@@ -191,11 +200,17 @@ __global__ void __launch_bounds__(256, 6) k_dec_strip(Batch B) {
     __syncwarp();
     if (quarter == 3 && ch) rowcarry[row] = (uint8_t)cf;      // carry into the next tile
 
-    // 5. restore and store
+    // 5. restore and store: per word one byte permute gives every byte the field of the
+    //    last label-1 byte at or before it (selector table by label pattern), or the
+    //    carried field (the second operand) when there is none
     if (valid > 0) {
-      const uint32_t C4 = in_fld * 0x01010101u;
+      uint32_t carry4 = in_fld * 0x01010101u;
 #pragma unroll
-      for (int i = 0; i < 4; i++) v[i] = (v[i] & ~FM4) | xf[i] | (~mm[i] & C4);
+      for (int i = 0; i < 4; i++) {
+        const uint32_t f = __byte_perm(v[i] & FM4, carry4, fillsel[zw[i]]);
+        v[i] = (v[i] & ~FM4) | f;
+        carry4 = __byte_perm(f, 0u, 0x3333u);
+      }
       uint8_t* dst = d.dst + (size_t)y * W + x;
       if (valid == 16 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
         *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
