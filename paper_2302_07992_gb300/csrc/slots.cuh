@@ -273,25 +273,26 @@ __device__ __forceinline__ void spread_slots(uint32_t (&px)[8], uint32_t zmask, 
 // Receiver: gather the slot fields of my 32 pixels into the chunk-local MSB-first
 // stream sbuf at bit my_off.  Per 4-pixel word one byte permute puts the j-th label-0
 // pixel in byte 3 - j; masked to the field bits, the fields are packed most-significant
-// first by multiply-adds (byte j moves up by (4 - j)(8 - s)) and appended to a word
+// first by multiply-adds (byte j's field moves up by (4 - j)(8 - s) - fshift) and appended to a word
 // that is stored once full: the words wholly inside my range are plain stores, the two
 // I share with my neighbours are OR-ed (the caller cleared the range).
 __device__ __forceinline__ void gather_slots(const uint32_t (&px)[8], uint32_t zmask, uint32_t slots,
                                              uint32_t fshift, uint32_t my_off, uint32_t* sbuf,
                                              const SlotTables& T, uint32_t* err) {
-  const uint32_t fmask = (1u << slots) - 1u;
-  const uint32_t FREP = fmask * 0x01010101u;
+  const uint32_t FM = ((1u << slots) - 1u) << fshift;             // the field inside a byte
   const uint32_t dsh = 8u - slots;
-  const uint32_t v3 = 1u << dsh, v2 = v3 << dsh, v1 = v2 << dsh, v0 = v1 << dsh;
+  // byte j's field (at bit fshift) moves up by (4 - j)(8 - s) - fshift, which is >= 0
+  // since fshift <= 8 - s: the field's offset inside its byte is folded into v0..v3
+  const uint32_t v3 = (1u << dsh) >> fshift, v2 = v3 << dsh, v1 = v2 << dsh, v0 = v1 << dsh;
   uint32_t wi = my_off >> 5, c = my_off & 31, word = 0;
   bool first = true;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
     const uint32_t nb = (uint32_t)__popc(zw) * slots;
-    const uint32_t fld = (__byte_perm(px[i], 0, T.compact_rev[zw]) >> fshift) & FREP;
-    const uint32_t P = (fld & 0xFFu) * v0 + (fld & 0xFF00u) * v1 + (fld & 0xFF0000u) * v2 +
-                       (fld & 0xFF000000u) * v3;                 // nb bits, left-aligned
+    const uint32_t fld = __byte_perm(px[i], 0, T.compact_rev[zw]);
+    const uint32_t P = (fld & FM) * v0 + (fld & (FM << 8)) * v1 + (fld & (FM << 16)) * v2 +
+                       (fld & (FM << 24)) * v3;                  // nb bits, left-aligned
     word |= P >> c;
     c += nb;
     if (c >= 32) {
