@@ -126,12 +126,6 @@ __host__ __device__ __forceinline__ uint32_t sel_compact_rev(uint32_t z) {
     if ((z >> q) & 1u) { sel = (sel & ~(0xFu << (4 * (3 - j)))) | ((uint32_t)q << (4 * (3 - j))); j++; }
   return sel;
 }
-// 0xFF in the bytes of the label-0 pixels of pattern z
-__host__ __device__ __forceinline__ uint32_t zero_bytes(uint32_t z) {
-  return ((z & 1u) ? 0xFFu : 0u) | ((z & 2u) ? 0xFF00u : 0u) | ((z & 4u) ? 0xFF0000u : 0u) |
-         ((z & 8u) ? 0xFF000000u : 0u);
-}
-
 // Block-wide exclusive scan of one value per thread (256 threads); returns the
 // exclusive prefix and the block total.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t& total) {
@@ -190,7 +184,7 @@ constexpr int Z2BUF_WORDS = ((SBUF_WORDS + 15) / 16 + 2) * 16;
 
 // Tables of byte-permute selectors, one entry per 4-pixel label-0 pattern.
 struct SlotTables {
-  uint32_t expand[16], expand_rev[16], compact_rev[16], zb[16];
+  uint32_t expand[16], expand_rev[16], compact_rev[16];
 };
 __device__ __forceinline__ void init_slot_tables(SlotTables& T) {
   const int t = threadIdx.x;
@@ -198,7 +192,6 @@ __device__ __forceinline__ void init_slot_tables(SlotTables& T) {
     T.expand[t] = sel_expand(t);
     T.expand_rev[t] = sel_expand_rev(t);
     T.compact_rev[t] = sel_compact_rev(t);
-    T.zb[t] = zero_bytes(t);
   }
 }
 
@@ -231,8 +224,9 @@ __device__ __forceinline__ void spread_slots(uint32_t (&px)[8], uint32_t zmask, 
       const uint32_t Ew = __funnelshift_l(sbuf[w + 1], sbuf[w], idx & 31);
       const uint32_t F = Ew >> (32 - 4 * slots);                  // f0 .. f3, right-aligned
       const uint32_t cons = (F & fmask) * u0 + (F & m1) * u1 + (F & m2) * u2 + (F & m3) * u3;
-      const uint32_t m = T.zb[zw] & FREP;
-      px[i] = (px[i] & ~m) | __byte_perm(cons, 0, T.expand_rev[zw]);
+      const uint32_t sel = T.expand_rev[zw];
+      const uint32_t m = __byte_perm(FREP, 0, sel);                 // the field bits of the slot pixels
+      px[i] = (px[i] & ~m) | __byte_perm(cons, 0, sel);
       idx += (uint32_t)__popc(zw) * slots;
     }
   } else if (zmask && k0 < E) {
