@@ -43,6 +43,24 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
 
 // 20 CTAs per SM (48 registers) measured slightly faster than the unbounded build
 // (56-63 registers) and than 12
+// Row partial sums at level SH + 2 (2^SH keystream words per 2-bit lane), the shift a
+// compile-time constant so that the loop's lane tests and shifts fold away.
+template <int SH>
+__device__ __forceinline__ uint64_t level_partial(const uint32_t (&sw)[16]) {
+  uint64_t v = 0;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    acc += sw[i] & 0x03030303u;                            // byte lanes, <= 12 each
+    if (((i + 1) & ((1 << SH) - 1)) == 0) {
+      const uint32_t lanev = ((acc * 0x01010101u) >> 24) & 3u;   // sum of the 4 bytes, mod 4
+      v |= (uint64_t)lanev << (2 * (i >> SH));
+      acc = 0;
+    }
+  }
+  return v;
+}
+
 template <int MODE, bool GENERAL, bool ANY_MED>
 __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
@@ -310,18 +328,12 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
       else vlo = push_nibble(vlo, x);
     }
     v = ((uint64_t)vhi << 32) | vlo;
+  } else if (Ls == 2) {
+    v = level_partial<0>(sw);
+  } else if (Ls == 3) {
+    v = level_partial<1>(sw);
   } else {
-    const int sh = Ls - 2;                                 // 2^sh words per lane
-    uint32_t acc = 0;
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-      acc += sw[i] & 0x03030303u;                          // byte lanes, <= 12 each
-      if (((i + 1) & ((1 << sh) - 1)) == 0) {
-        const uint32_t lanev = ((acc * 0x01010101u) >> 24) & 3u;   // sum of the 4 bytes, mod 4
-        v |= (uint64_t)lanev << (2 * (i >> sh));
-        acc = 0;
-      }
-    }
+    v = level_partial<2>(sw);
   }
   for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
   __syncthreads();   // sub[] cleared
