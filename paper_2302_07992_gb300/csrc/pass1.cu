@@ -43,6 +43,11 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
 
 // 20 CTAs per SM (48 registers) measured slightly faster than the unbounded build
 // (56-63 registers) and than 12
+template <int N>
+struct LevelTag {
+  static constexpr int value = N;
+};
+
 // Row partial sums at level SH + 2 (2^SH keystream words per 2-bit lane), the shift a
 // compile-time constant so that the loop's lane tests and shifts fold away.
 template <int SH>
@@ -313,66 +318,72 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
   // (LMR's default lmin is 4).  Row partial at level Ls: lane k (2 bits, bits 2k..2k+1) =
   // sum over the row's columns [k 2^Ls, (k+1) 2^Ls) of s mod 4.
   const int lmin = d.lmin;
-  const int Ls = lmin < 1 ? 1 : (lmin > 4 ? 4 : lmin);
-  uint64_t v = 0;
-  if (Ls == 1) {
-    // per word: (t * 0x101) has c0+c1 in byte 1 and c2+c3 in byte 3 (each <= 6, no
-    // carries between bytes); their low two bits move to bits 28..29 and 30..31 with
-    // one more multiply (bits 8 -> 28 by 2^20, bits 24 -> 30 by 2^6), then shift in
-    uint32_t vlo = 0, vhi = 0;
-#pragma unroll
-    for (int i = 15; i >= 0; i--) {
-      const uint32_t u = (sw[i] & 0x03030303u) * 0x0101u;
-      const uint32_t x = (u & 0x03000300u) * 0x00100040u;
-      if (i >= 8) vhi = push_nibble(vhi, x);
-      else vlo = push_nibble(vlo, x);
-    }
-    v = ((uint64_t)vhi << 32) | vlo;
-  } else if (Ls == 2) {
-    v = level_partial<0>(sw);
-  } else if (Ls == 3) {
-    v = level_partial<1>(sw);
-  } else {
-    v = level_partial<2>(sw);
-  }
-  for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
-  __syncthreads();   // sub[] cleared
-  const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
-  const int cov_cols = W - x0;
-  // unrolled over the six levels: sizes, masks and store widths are constants per level
-#pragma unroll
-  for (int L = 1; L <= 6; L++) {
-    if (L < Ls) continue;                                  // entries stay 0 (sub[] cleared)
-    if (L > Ls) v = pair4(v);                              // widen the columns
-    if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
-    else {
-      if (lane == 0) l6_part[warp] = v;
-      __syncthreads();
-      v = add4(l6_part[0], l6_part[1]);
-    }
-    const int nb = TILE >> L;                              // blocks per side at this level
-    const int br = r >> L;
-    if ((r & ((1 << L) - 1)) == 0) {
-      uint64_t ang = v;
-      // angle 0 for levels below lmin and for blocks not entirely inside the image
-      const bool row_cov = (br + 1) * (1 << L) <= cov_rows;
-      int ncol = cov_cols >> L;
-      if (ncol > nb) ncol = nb;
-      if (L < lmin || !row_cov || ncol <= 0) ang = 0;
-      else if (ncol < nb) ang &= (1ull << (2 * ncol)) - 1ull;
-      // one block row = 2 nb bits at byte subtree_off(L) + br * nb / 4
-      if (L == 1) *reinterpret_cast<uint64_t*>(sub + br * 8) = ang;
-      else if (L == 2) *reinterpret_cast<uint32_t*>(sub + subtree_off(2) + br * 4) = (uint32_t)ang;
-      else if (L == 3) *reinterpret_cast<uint16_t*>(sub + subtree_off(3) + br * 2) = (uint16_t)ang;
-      else if (L == 4) sub[subtree_off(4) + br] = (uint8_t)ang;
-      else {
-        const int off = subtree_off(L) * 8 + br * 2 * nb;   // 4 or 2 bits: shared bytes, OR-ed in
-        atomicOr(reinterpret_cast<unsigned int*>(sub) + (off >> 5),
-                 (uint32_t)(ang & ((1u << (2 * nb)) - 1)) << (off & 31));
+  // the starting level as a compile-time constant: the partial sums, the row shuffles
+  // and the level loop's tests fold for each of the four starting levels
+  auto levels = [&](auto ls_tag) {
+    constexpr int Ls = decltype(ls_tag)::value;
+    uint64_t v = 0;
+    if constexpr (Ls == 1) {
+      // per word: (t * 0x101) has c0+c1 in byte 1 and c2+c3 in byte 3 (each <= 6, no
+      // carries between bytes); their low two bits move to bits 28..29 and 30..31 with
+      // one more multiply (bits 8 -> 28 by 2^20, bits 24 -> 30 by 2^6), then shift in
+      uint32_t vlo = 0, vhi = 0;
+  #pragma unroll
+      for (int i = 15; i >= 0; i--) {
+        const uint32_t u = (sw[i] & 0x03030303u) * 0x0101u;
+        const uint32_t x = (u & 0x03000300u) * 0x00100040u;
+        if (i >= 8) vhi = push_nibble(vhi, x);
+        else vlo = push_nibble(vlo, x);
       }
+      v = ((uint64_t)vhi << 32) | vlo;
+    } else {
+      v = level_partial<Ls - 2>(sw);
     }
-    if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v & 3u);  // raw tile sum for the top levels
-  }
+  #pragma unroll
+    for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
+    __syncthreads();   // sub[] cleared
+    const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
+    const int cov_cols = W - x0;
+    // unrolled over the six levels: sizes, masks and store widths are constants per level
+  #pragma unroll
+    for (int L = 1; L <= 6; L++) {
+      if (L < Ls) continue;                                  // entries stay 0 (sub[] cleared)
+      if (L > Ls) v = pair4(v);                              // widen the columns
+      if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
+      else {
+        if (lane == 0) l6_part[warp] = v;
+        __syncthreads();
+        v = add4(l6_part[0], l6_part[1]);
+      }
+      const int nb = TILE >> L;                              // blocks per side at this level
+      const int br = r >> L;
+      if ((r & ((1 << L) - 1)) == 0) {
+        uint64_t ang = v;
+        // angle 0 for levels below lmin and for blocks not entirely inside the image
+        const bool row_cov = (br + 1) * (1 << L) <= cov_rows;
+        int ncol = cov_cols >> L;
+        if (ncol > nb) ncol = nb;
+        if (L < lmin || !row_cov || ncol <= 0) ang = 0;
+        else if (ncol < nb) ang &= (1ull << (2 * ncol)) - 1ull;
+        // one block row = 2 nb bits at byte subtree_off(L) + br * nb / 4
+        if (L == 1) *reinterpret_cast<uint64_t*>(sub + br * 8) = ang;
+        else if (L == 2) *reinterpret_cast<uint32_t*>(sub + subtree_off(2) + br * 4) = (uint32_t)ang;
+        else if (L == 3) *reinterpret_cast<uint16_t*>(sub + subtree_off(3) + br * 2) = (uint16_t)ang;
+        else if (L == 4) sub[subtree_off(4) + br] = (uint8_t)ang;
+        else {
+          const int off = subtree_off(L) * 8 + br * 2 * nb;   // 4 or 2 bits: shared bytes, OR-ed in
+          atomicOr(reinterpret_cast<unsigned int*>(sub) + (off >> 5),
+                   (uint32_t)(ang & ((1u << (2 * nb)) - 1)) << (off & 31));
+        }
+      }
+      if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v & 3u);  // raw tile sum for the top levels
+    }
+  };
+  const int ls_rt = lmin < 1 ? 1 : (lmin > 4 ? 4 : lmin);   // uniform over the CTA (one tile)
+  if (ls_rt == 1) levels(LevelTag<1>());
+  else if (ls_rt == 2) levels(LevelTag<2>());
+  else if (ls_rt == 3) levels(LevelTag<3>());
+  else levels(LevelTag<4>());
   __syncthreads();
   // subtree to global (352 bytes)
   {
