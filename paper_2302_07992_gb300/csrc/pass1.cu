@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
       // carries between bytes); their low two bits move to bits 28..29 and 30..31 with
       // one more multiply (bits 8 -> 28 by 2^20, bits 24 -> 30 by 2^6), then shift in
       uint32_t vlo = 0, vhi = 0;
-  #pragma unroll
+#pragma unroll
       for (int i = 15; i >= 0; i--) {
         const uint32_t u = (sw[i] & 0x03030303u) * 0x0101u;
         const uint32_t x = (u & 0x03000300u) * 0x00100040u;
@@ -339,13 +339,13 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
     } else {
       v = level_partial<Ls - 2>(sw);
     }
-  #pragma unroll
+#pragma unroll
     for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
     __syncthreads();   // sub[] cleared
     const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
     const int cov_cols = W - x0;
     // unrolled over the six levels: sizes, masks and store widths are constants per level
-  #pragma unroll
+#pragma unroll
     for (int L = 1; L <= 6; L++) {
       if (L < Ls) continue;                                  // entries stay 0 (sub[] cleared)
       if (L > Ls) v = pair4(v);                              // widen the columns
