@@ -341,18 +341,24 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
       __syncthreads();
       gather_slots(cur.px, zmask, slots, fshift, my_off, sbuf, tabs, B.err);
       __syncthreads();
-      const uint64_t zbase = 16 * Jb;                        // word index of z2buf[0]
-      for (uint64_t w = wa + t; w <= wb; w += HIDE_THREADS) {
-        const uint64_t b0 = 32 * w;
-        const uint64_t lo = b0 > Gc ? b0 : Gc, hi = b0 + 32 < endc ? b0 + 32 : endc;   // my bits of word w
-        if (!RDHEI_IDX_OK(B.err, w < out_words && ((lo - Gc) >> 5) + 1 < SBUF_WORDS &&
-                                     w - zbase < (uint64_t)(16 * Z2_WINDOW_BLOCKS)))
+      // output words wa .. wb in 32-bit offsets from word wa: the chunk's stream starts
+      // g0 bits into word wa, so word wa + k is sbuf's words k - 1, k shifted right by g0
+      // (bits outside [Gc, endc) masked off)
+      const uint32_t nwords = (uint32_t)(wb - wa) + 1;
+      const uint32_t g0 = (uint32_t)(Gc & 31), e = (uint32_t)(endc - 32 * wa);
+      const uint32_t zoff = (uint32_t)(wa - 16 * Jb);              // z2buf word of output word wa
+      uint32_t* const outw = out + wa;
+      for (uint32_t k = t; k < nwords; k += HIDE_THREADS) {
+        const uint32_t b0 = 32 * k;
+        const uint32_t lo = b0 > g0 ? b0 : g0, hi = b0 + 32 < e ? b0 + 32 : e;   // my bits of word wa + k
+        if (!RDHEI_IDX_OK(B.err, wa + k < out_words && k < SBUF_WORDS &&
+                                     zoff + k < (uint32_t)(16 * Z2_WINDOW_BLOCKS)))
           continue;
-        const uint32_t raw = get_bits(sbuf, (uint32_t)(lo - Gc), (uint32_t)(hi - lo)) << (uint32_t)(b0 + 32 - hi);
-        const uint32_t keep = (0xFFFFFFFFu >> (uint32_t)(lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (uint32_t)(hi - b0));
-        const uint32_t v = bswap32(raw) ^ (z2buf[w - zbase] & bswap32(keep));
-        if (lo == b0 && hi == b0 + 32) out[w] = v;
-        else atomicOr(out + w, v);
+        const uint32_t x = __funnelshift_r(sbuf[k], k > 0 ? sbuf[k - 1] : 0u, g0);
+        const uint32_t keep = (0xFFFFFFFFu >> (lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (hi - b0));
+        const uint32_t v = bswap32(x & keep) ^ (z2buf[zoff + k] & bswap32(keep));
+        if (lo == b0 && hi == b0 + 32) outw[k] = v;
+        else atomicOr(outw + k, v);
       }
     }
     Gc += Tc;
