@@ -221,15 +221,19 @@ __global__ void __launch_bounds__(HIDE_THREADS, EXTRACT ? 5 : 4) k_scan(Batch B)
       const uint64_t end = umin64(G + T, E);
       uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
       if (end > G) {
-        const uint64_t w_hi = (end - 1) >> 5;
-        for (uint64_t w = w_lo + t; w <= w_hi; w += HIDE_THREADS) {
-          const uint64_t b0 = 32 * w;
-          const uint64_t lo = b0 > G ? b0 : G, hi = b0 + 32 < end ? b0 + 32 : end;   // my bits of word w
-          if (!RDHEI_IDX_OK(B.err, w < ((d.max_bits + 31) >> 5) && ((lo - G) >> 5) + 1 < SBUF_WORDS)) continue;
-          uint32_t raw = get_bits(sbuf, (uint32_t)(lo - G), (uint32_t)(hi - lo));
-          raw <<= (uint32_t)(b0 + 32 - hi);
-          if (lo == b0 && hi == b0 + 32) out[w] = bswap32(raw);
-          else atomicOr(out + w, bswap32(raw));
+        // in 32-bit offsets from word w_lo, as in the fused extraction: word w_lo + k is
+        // sbuf's words k - 1, k shifted right by G's offset inside word w_lo
+        const uint32_t nwords = (uint32_t)(((end - 1) >> 5) - w_lo) + 1;
+        const uint32_t g0 = (uint32_t)(G & 31), e = (uint32_t)(end - 32 * w_lo);
+        uint32_t* const outw = out + w_lo;
+        for (uint32_t k = t; k < nwords; k += HIDE_THREADS) {
+          const uint32_t b0 = 32 * k;
+          const uint32_t lo = b0 > g0 ? b0 : g0, hi = b0 + 32 < e ? b0 + 32 : e;   // my bits of word w_lo + k
+          if (!RDHEI_IDX_OK(B.err, w_lo + k < ((d.max_bits + 31) >> 5) && k < SBUF_WORDS)) continue;
+          const uint32_t x = __funnelshift_r(sbuf[k], k > 0 ? sbuf[k - 1] : 0u, g0);
+          const uint32_t keep = (0xFFFFFFFFu >> (lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (hi - b0));
+          if (lo == b0 && hi == b0 + 32) outw[k] = bswap32(x);
+          else atomicOr(outw + k, bswap32(x & keep));
         }
       }
     }
