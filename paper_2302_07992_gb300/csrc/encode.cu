@@ -548,33 +548,39 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
   const StripRange r = strip_range(B, s, d);
   __syncthreads();   // tables; the first window (written before phase 1's first barrier)
   if (r.G0 >= r.send) return;
-  uint64_t Wb = r.G0 >> 5;                                   // the staged window: words [Wb, Wb + Wn)
+  const uint64_t Wb = r.G0 >> 5;                             // the first staged window: words [Wb, Wb + Wn)
   uint32_t Wn = window_words(Wb, r.send);
   const uint32_t slots = (uint32_t)slots_of(d, info);
   const uint32_t fshift = (d.variant == RDHEI_LMR ? 7u : 8u) - slots;
-  uint64_t Gc = r.G0;
-  for (uint64_t c0 = p0; c0 < p1 && Gc < r.send; c0 += SCAN_PX) {
+  // 32-bit positions: pixels from the strip's first, stream bits from B0, the start of
+  // the first window's first word (the strip holds < 2^22 pixels of <= 7 slot bits)
+  const uint64_t B0 = 32 * Wb;
+  uint8_t* const sdst = d.dst + p0;
+  const uint32_t npx = (uint32_t)(p1 - p0), send = (uint32_t)(r.send - B0);
+  uint32_t wb = 0;                                           // the window's first word, relative to Wb
+  uint32_t g = (uint32_t)(r.G0 - B0);
+  for (uint32_t c0 = 0; c0 < npx && g < send; c0 += SCAN_PX) {
     ChunkPx cur;
-    const uint64_t q0 = c0 + (uint64_t)HIDE_PX * t;
-    load_run(d, d.dst, q0, p1, true, cur);
+    const uint32_t q0 = c0 + (uint32_t)HIDE_PX * t;
+    load_strip_run(d, sdst, p0, q0, npx, cur);
     const uint32_t zmask = zero_mask(d, cur);
     uint32_t Tc;
     const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, sm.warp_tot, Tc);
-    const uint64_t endc = umin64(Gc + Tc, r.send);
-    if (endc > Gc) {
-      const uint64_t w_lo = Gc >> 5;
-      if (((endc - 1) >> 5) >= Wb + Wn) {
+    const uint32_t endc = min(g + Tc, send);
+    if (endc > g) {
+      const uint32_t w_lo = g >> 5;
+      if (((endc - 1) >> 5) >= wb + Wn) {
         // the chunk's slots run past the window: the next window starts at its first word
         // (the block scan's barriers ordered every earlier read of the buffer)
-        Wb = w_lo;
-        Wn = window_words(Wb, r.send);
-        stage_message(d, Wb, Wn, sm.ebuf);
+        wb = w_lo;
+        Wn = window_words(Wb + wb, r.send);
+        stage_message(d, Wb + wb, Wn, sm.ebuf);
         __syncthreads();
       }
-      const uint64_t k0 = Gc + my_off;
+      const uint32_t k0 = g + my_off;
       if (zmask && k0 < endc) {
-        spread_slots(cur.px, zmask, slots, fshift, sm.ebuf + (w_lo - Wb), 32 * w_lo, k0, endc, sm.tabs, B.err);
-        uint8_t* dst = d.dst + q0;
+        spread_slots(cur.px, zmask, slots, fshift, sm.ebuf + (w_lo - wb), 32 * w_lo, k0, endc, sm.tabs, B.err);
+        uint8_t* dst = sdst + q0;
         if (cur.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
           __stcg(reinterpret_cast<uint4*>(dst), make_uint4(cur.px[0], cur.px[1], cur.px[2], cur.px[3]));
           __stcg(reinterpret_cast<uint4*>(dst) + 1, make_uint4(cur.px[4], cur.px[5], cur.px[6], cur.px[7]));
@@ -585,7 +591,7 @@ __device__ __forceinline__ void embed_strip(const Batch& B, uint32_t s, EmbedSme
         }
       }
     }
-    Gc += Tc;
+    g += Tc;
   }
 }
 

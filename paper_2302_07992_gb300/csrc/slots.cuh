@@ -177,6 +177,32 @@ __device__ __forceinline__ void load_run(const ImgDesc& d, const uint8_t* img, u
   }
 }
 
+// The same for 32 pixels at strip-relative offset q0 of a strip of n pixels whose first
+// pixel is strip[0] (image pixel p0): 32-bit offsets, coherent loads (the fused kernel
+// reads back the strip it has just written).
+__device__ __forceinline__ void load_strip_run(const ImgDesc& d, const uint8_t* strip, uint64_t p0, uint32_t q0,
+                                               uint32_t n, ChunkPx& r) {
+  r.valid = q0 < n ? (int)min((uint32_t)HIDE_PX, n - q0) : 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r.px[i] = 0;
+  r.lbits = 0xFFFFFFFFu;
+  const uint8_t* src = strip + q0;
+  if (r.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    const uint4 a = __ldcg(s4), e = __ldcg(s4 + 1);
+    r.px[0] = a.x; r.px[1] = a.y; r.px[2] = a.z; r.px[3] = a.w;
+    r.px[4] = e.x; r.px[5] = e.y; r.px[6] = e.z; r.px[7] = e.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < HIDE_PX; k++)
+      if (k < r.valid) r.px[k >> 2] |= (uint32_t)__ldcg(src + k) << (8 * (k & 3));
+  }
+  if (d.variant == RDHEI_LMR && r.valid > 0) {
+    const uint64_t nw = ((uint64_t)d.H * d.W + 31) >> 5;
+    r.lbits = stream_bits32_cg(d.map_bits, nw, p0 + q0);
+  }
+}
+
 // Staging for the fused kernels' K2 keystream: enough 16-word ChaCha20 blocks for the
 // message words of one chunk (at most 7 * 8192 bits) plus the two partial blocks at
 // its ends.
@@ -200,8 +226,11 @@ __device__ __forceinline__ void init_slot_tables(SlotTables& T) {
 // 32), and one zero word past the last one needed; my first slot is stream bit k0 and
 // stream bits at or past E (the end of the message) are not written: those slots keep
 // their pixel bits.
+// POS is the type of the stream positions: 64-bit absolute ones, or 32-bit ones relative
+// to a strip (the fused kernel), which cost fewer instructions.
+template <typename POS>
 __device__ __forceinline__ void spread_slots(uint32_t (&px)[8], uint32_t zmask, uint32_t slots, uint32_t fshift,
-                                             const uint32_t* sbuf, uint64_t sb0, uint64_t k0, uint64_t E,
+                                             const uint32_t* sbuf, POS sb0, POS k0, POS E,
                                              const SlotTables& T, uint32_t* err) {
   const uint32_t fmask = (1u << slots) - 1u;
   const uint32_t FREP = (fmask << fshift) * 0x01010101u;
@@ -234,13 +263,13 @@ __device__ __forceinline__ void spread_slots(uint32_t (&px)[8], uint32_t zmask, 
     // once, spread the fields to consecutive bytes, then move them to their pixels
     // with one byte permute; the slots past the message end keep their bits
     const uint32_t s2 = 2 * slots, s3 = 3 * slots;
-    uint64_t k = k0;
+    POS k = k0;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       const uint32_t zw = (zmask >> (4 * i)) & 0xFu;
       const uint32_t nb = (uint32_t)__popc(zw) * slots;           // <= 28 bits
       if (nb && k < E && RDHEI_IDX_OK(err, ((k - sb0) >> 5) + 1 < SBUF_WORDS)) {
-        const uint32_t avail = (uint32_t)umin64(nb, E - k);
+        const uint32_t avail = (POS)nb < E - k ? nb : (uint32_t)(E - k);
         const uint32_t Ew = get_bits(sbuf, (uint32_t)(k - sb0), avail) << (32 - avail);   // left-aligned
         const uint32_t rs = 32 - slots;
         const uint32_t cons = (Ew >> rs) | (((Ew << slots) >> rs) << 8) | (((Ew << s2) >> rs) << 16) |
