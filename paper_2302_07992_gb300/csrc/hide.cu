@@ -311,51 +311,58 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   uint32_t* out = reinterpret_cast<uint32_t*>(d.bits_out);
   const uint64_t out_words = (d.max_bits + 31) >> 5;
   (void)out_words;                                           // index checks only
+  // 32-bit positions: pixels from the part's first (p0), stream bits from 32 W0, the
+  // start of the word holding its first slot bit; K2 blocks from J0 = W0 / 16
+  const uint64_t W0 = G0 >> 5, J0 = W0 >> 4;
+  const uint32_t o0 = (uint32_t)(W0 & 15);                    // W0's word inside block J0
+  const uint8_t* const ssrc = d.src + p0;
+  const uint32_t npx = (uint32_t)(p1 - p0), send_r = (uint32_t)(send - 32 * W0);
+  uint32_t* const outp = out + W0;
   ChunkPx cur;
-  load_run(d, d.src, p0 + (uint64_t)HIDE_PX * t, p1, false, cur);
-  // the strip's first keystream window, while the first chunk's loads are in flight
-  uint64_t Jb = (G0 >> 5) >> 4;                              // window: blocks [Jb, Jb + Jn)
-  uint32_t Jn = z2_window(Jb, send);
-  z2_blocks(d, Jb, Jn, z2buf);
+  load_strip_run<false>(d, ssrc, p0, (uint32_t)HIDE_PX * t, npx, cur);
+  // the part's first keystream window, while the first chunk's loads are in flight
+  uint32_t jb = 0;                                           // window: blocks [J0 + jb, J0 + jb + Jn)
+  uint32_t Jn = z2_window(J0, send);
+  z2_blocks(d, J0, Jn, z2buf);
   __syncthreads();   // tables, keystream
-  uint64_t Gc = G0;
-  for (uint64_t c0 = p0; c0 < p1 && Gc < send; c0 += SCAN_PX) {
+  uint32_t g = (uint32_t)(G0 & 31);
+  for (uint32_t c0 = 0; c0 < npx && g < send_r; c0 += SCAN_PX) {
     ChunkPx nxt;                                             // next chunk in flight
-    load_run(d, d.src, c0 + SCAN_PX + (uint64_t)HIDE_PX * t, p1, false, nxt);
+    load_strip_run<false>(d, ssrc, p0, c0 + SCAN_PX + (uint32_t)HIDE_PX * t, npx, nxt);
     const uint32_t zmask = zero_mask(d, cur);
     uint32_t Tc;
     const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, warp_tot, Tc);
-    const uint64_t endc = umin64(Gc + Tc, send);
-    if (endc > Gc) {
+    const uint32_t endc = min(g + Tc, send_r);
+    if (endc > g) {
       for (int i = t; i < (int)((Tc >> 5) + 2) && i < SBUF_WORDS; i += HIDE_THREADS) sbuf[i] = 0u;
-      const uint64_t wa = Gc >> 5, wb = (endc - 1) >> 5;
-      if ((wb >> 4) >= Jb + Jn) {
+      const uint32_t wa = g >> 5, wb = (endc - 1) >> 5;       // words, from W0
+      if (((o0 + wb) >> 4) >= jb + Jn) {
         // the chunk's words run past the window: the next window starts at its first block
         // (the block scan's barriers ordered every earlier read of z2buf)
-        Jb = wa >> 4;
-        Jn = z2_window(Jb, send);
-        z2_blocks(d, Jb, Jn, z2buf);
+        jb = (o0 + wa) >> 4;
+        Jn = z2_window(J0 + jb, send);
+        z2_blocks(d, J0 + jb, Jn, z2buf);
       }
       // a word that starts inside this chunk and ends inside the next one of this part
       // is cleared here, before the ORs of both; the word holding the part's end (shared
       // with the next part or strip, or the last one) was cleared by k_topmap
-      if (t == 0 && (endc & 31) && ((endc >> 5) << 5) >= Gc && (endc >> 5) < (send >> 5) &&
-          RDHEI_IDX_OK(B.err, (endc >> 5) < out_words))
-        out[endc >> 5] = 0u;
+      if (t == 0 && (endc & 31) && ((endc >> 5) << 5) >= g && (endc >> 5) < (send_r >> 5) &&
+          RDHEI_IDX_OK(B.err, W0 + (endc >> 5) < out_words))
+        outp[endc >> 5] = 0u;
       __syncthreads();
       gather_slots(cur.px, zmask, slots, fshift, my_off, sbuf, tabs, B.err);
       __syncthreads();
-      // output words wa .. wb in 32-bit offsets from word wa: the chunk's stream starts
-      // g0 bits into word wa, so word wa + k is sbuf's words k - 1, k shifted right by g0
-      // (bits outside [Gc, endc) masked off)
-      const uint32_t nwords = (uint32_t)(wb - wa) + 1;
-      const uint32_t g0 = (uint32_t)(Gc & 31), e = (uint32_t)(endc - 32 * wa);
-      const uint32_t zoff = (uint32_t)(wa - 16 * Jb);              // z2buf word of output word wa
-      uint32_t* const outw = out + wa;
+      // output words wa .. wb: the chunk's stream starts g0 bits into word wa, so word
+      // wa + k is sbuf's words k - 1, k shifted right by g0 (bits outside [g, endc)
+      // masked off)
+      const uint32_t nwords = wb - wa + 1;
+      const uint32_t g0 = g & 31, e = endc - 32 * wa;
+      const uint32_t zoff = o0 + wa - 16 * jb;                  // z2buf word of output word wa
+      uint32_t* const outw = outp + wa;
       for (uint32_t k = t; k < nwords; k += HIDE_THREADS) {
         const uint32_t b0 = 32 * k;
         const uint32_t lo = b0 > g0 ? b0 : g0, hi = b0 + 32 < e ? b0 + 32 : e;   // my bits of word wa + k
-        if (!RDHEI_IDX_OK(B.err, wa + k < out_words && k < SBUF_WORDS &&
+        if (!RDHEI_IDX_OK(B.err, W0 + wa + k < out_words && k < SBUF_WORDS &&
                                      zoff + k < (uint32_t)(16 * Z2_WINDOW_BLOCKS)))
           continue;
         const uint32_t x = __funnelshift_r(sbuf[k], k > 0 ? sbuf[k - 1] : 0u, g0);
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
         else atomicOr(outw + k, v);
       }
     }
-    Gc += Tc;
+    g += Tc;
     cur = nxt;
   }
 }

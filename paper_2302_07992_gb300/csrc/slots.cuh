@@ -178,8 +178,9 @@ __device__ __forceinline__ void load_run(const ImgDesc& d, const uint8_t* img, u
 }
 
 // The same for 32 pixels at strip-relative offset q0 of a strip of n pixels whose first
-// pixel is strip[0] (image pixel p0): 32-bit offsets, coherent loads (the fused kernel
-// reads back the strip it has just written).
+// pixel is strip[0] (image pixel p0), in 32-bit offsets.  COHERENT: L2 loads (the fused
+// encode reads back the strip it has just written), else streaming loads.
+template <bool COHERENT = true>
 __device__ __forceinline__ void load_strip_run(const ImgDesc& d, const uint8_t* strip, uint64_t p0, uint32_t q0,
                                                uint32_t n, ChunkPx& r) {
   r.valid = q0 < n ? (int)min((uint32_t)HIDE_PX, n - q0) : 0;
@@ -189,17 +190,17 @@ __device__ __forceinline__ void load_strip_run(const ImgDesc& d, const uint8_t* 
   const uint8_t* src = strip + q0;
   if (r.valid == HIDE_PX && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
-    const uint4 a = __ldcg(s4), e = __ldcg(s4 + 1);
+    const uint4 a = COHERENT ? __ldcg(s4) : __ldcs(s4), e = COHERENT ? __ldcg(s4 + 1) : __ldcs(s4 + 1);
     r.px[0] = a.x; r.px[1] = a.y; r.px[2] = a.z; r.px[3] = a.w;
     r.px[4] = e.x; r.px[5] = e.y; r.px[6] = e.z; r.px[7] = e.w;
   } else {
 #pragma unroll
     for (int k = 0; k < HIDE_PX; k++)
-      if (k < r.valid) r.px[k >> 2] |= (uint32_t)__ldcg(src + k) << (8 * (k & 3));
+      if (k < r.valid) r.px[k >> 2] |= (uint32_t)(COHERENT ? __ldcg(src + k) : src[k]) << (8 * (k & 3));
   }
   if (d.variant == RDHEI_LMR && r.valid > 0) {
     const uint64_t nw = ((uint64_t)d.H * d.W + 31) >> 5;
-    r.lbits = stream_bits32_cg(d.map_bits, nw, p0 + q0);
+    r.lbits = COHERENT ? stream_bits32_cg(d.map_bits, nw, p0 + q0) : stream_bits32(d.map_bits, nw, p0 + q0);
   }
 }
 
