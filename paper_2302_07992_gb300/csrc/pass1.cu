@@ -35,6 +35,16 @@ __device__ __forceinline__ uint64_t pair4(uint64_t v) {
   s = (s | (s >> 16)) & 0x00000000FFFFFFFFull;
   return s;
 }
+// The same on 32-bit words: from level 2 on a 64-pixel row has at most 16 lanes.
+__device__ __forceinline__ uint32_t add4_32(uint32_t a, uint32_t b) { return a ^ b ^ ((a & b & 0x55555555u) << 1); }
+__device__ __forceinline__ uint32_t pair4_32(uint32_t v) {
+  const uint32_t M = 0x33333333u;
+  uint32_t s = ((v & M) + ((v >> 2) & M)) & M;
+  s = (s | (s >> 2)) & 0x0F0F0F0Fu;
+  s = (s | (s >> 4)) & 0x00FF00FFu;
+  s = (s | (s >> 8)) & 0x0000FFFFu;
+  return s;
+}
 __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
   uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
   uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
@@ -339,26 +349,40 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
     } else {
       v = level_partial<Ls - 2>(sw);
     }
+    // rows below level Ls; from level 2 on the lanes fit in 32 bits
+    uint32_t v32 = 0;
+    if constexpr (Ls == 1) {
+      v = add4(v, shfl_xor64(v, 1));                       // level 1: 32 lanes, row pairs
+    } else {
+      v32 = (uint32_t)v;
 #pragma unroll
-    for (int m = 0; m < Ls - 1; m++) v = add4(v, shfl_xor64(v, 1 << m));   // rows below level Ls
+      for (int m = 0; m < Ls - 1; m++) v32 = add4_32(v32, __shfl_xor_sync(0xffffffffu, v32, 1 << m));
+    }
     __syncthreads();   // sub[] cleared
-    const int cov_rows = H - ty * TILE;                      // rows of this tile inside the image
+    const int cov_rows = H - ty * TILE;                    // rows of this tile inside the image
     const int cov_cols = W - x0;
     // unrolled over the six levels: sizes, masks and store widths are constants per level
 #pragma unroll
     for (int L = 1; L <= 6; L++) {
-      if (L < Ls) continue;                                  // entries stay 0 (sub[] cleared)
-      if (L > Ls) v = pair4(v);                              // widen the columns
-      if (L <= 5) v = add4(v, shfl_xor64(v, 1 << (L - 1)));  // and the rows
-      else {
-        if (lane == 0) l6_part[warp] = v;
-        __syncthreads();
-        v = add4(l6_part[0], l6_part[1]);
+      if (L < Ls) continue;                                // entries stay 0 (sub[] cleared)
+      uint64_t ang;
+      if (L == 1) {
+        ang = v;                                           // (Ls == 1 here; rows summed above)
+      } else {
+        if (L == 2 && Ls == 1) v32 = (uint32_t)pair4(v);     // 32 lanes -> 16
+        else if (L > Ls) v32 = pair4_32(v32);              // widen the columns
+        if (L <= 5) {
+          v32 = add4_32(v32, __shfl_xor_sync(0xffffffffu, v32, 1 << (L - 1)));   // and the rows
+        } else {
+          if (lane == 0) l6_part[warp] = v32;
+          __syncthreads();
+          v32 = add4_32((uint32_t)l6_part[0], (uint32_t)l6_part[1]);
+        }
+        ang = v32;
       }
       const int nb = TILE >> L;                              // blocks per side at this level
       const int br = r >> L;
       if ((r & ((1 << L) - 1)) == 0) {
-        uint64_t ang = v;
         // angle 0 for levels below lmin and for blocks not entirely inside the image
         const bool row_cov = (br + 1) * (1 << L) <= cov_rows;
         int ncol = cov_cols >> L;
@@ -376,7 +400,7 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
                    (uint32_t)(ang & ((1u << (2 * nb)) - 1)) << (off & 31));
         }
       }
-      if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v & 3u);  // raw tile sum for the top levels
+      if (L == 6 && r == 0) B.sigma6[g] = (uint8_t)(v32 & 3u);  // raw tile sum for the top levels
     }
   };
   const int ls_rt = lmin < 1 ? 1 : (lmin > 4 ? 4 : lmin);   // uniform over the CTA (one tile)
