@@ -262,13 +262,19 @@ constexpr int Z2_WINDOW_BLOCKS = HIDE_THREADS;   // 256 keystream blocks = 4096 
 static_assert(16 * Z2_WINDOW_BLOCKS >= Z2BUF_WORDS, "a window holds one chunk's keystream");
 
 // keystream words of blocks [j0, j0 + nblk) into z2 (one block per thread)
+// Block t goes to words 16 t .. 16 t + 15 as four 16-byte stores, its 16-byte chunk q at
+// chunk q ^ ((t >> 1) & 3): the eight threads of a store phase then hit distinct banks
+// (plain layout: 16 threads per bank pair).  Word w of the window is read at z2_word(w).
+__device__ __forceinline__ uint32_t z2_word(uint32_t w) { return w ^ ((w >> 3) & 0xCu); }
 __device__ __forceinline__ void z2_blocks(const ImgDesc& d, uint64_t j0, uint32_t nblk, uint32_t* z2) {
   const int t = threadIdx.x;
   if ((uint32_t)t < nblk) {
     uint32_t o[16];
     chacha20_block<2>(d.k2, (uint32_t)(j0 + t), d.n2, o, d.one);
+    uint4* b = reinterpret_cast<uint4*>(z2 + 16 * t);
+    const int sw = (t >> 1) & 3;
 #pragma unroll
-    for (int i = 0; i < 16; i++) z2[16 * t + i] = o[i];
+    for (int q = 0; q < 4; q++) b[q ^ sw] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
   }
 }
 
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   __shared__ uint32_t sbuf[SBUF_WORDS];
-  __shared__ uint32_t z2buf[16 * Z2_WINDOW_BLOCKS];
+  __shared__ __align__(16) uint32_t z2buf[16 * Z2_WINDOW_BLOCKS];
   __shared__ uint32_t warp_tot[HIDE_THREADS / 32];
   __shared__ SlotTables tabs;
   const int t = threadIdx.x;
@@ -367,7 +373,7 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
           continue;
         const uint32_t x = __funnelshift_r(sbuf[k], k > 0 ? sbuf[k - 1] : 0u, g0);
         const uint32_t keep = (0xFFFFFFFFu >> (lo - b0)) & ~(hi - b0 >= 32 ? 0u : 0xFFFFFFFFu >> (hi - b0));
-        const uint32_t v = bswap32(x & keep) ^ (z2buf[zoff + k] & bswap32(keep));
+        const uint32_t v = bswap32(x & keep) ^ (z2buf[z2_word(zoff + k)] & bswap32(keep));
         if (lo == b0 && hi == b0 + 32) outw[k] = v;
         else atomicOr(outw + k, v);
       }
