@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
 #pragma unroll
       for (int i = 15; i >= 0; i--) {
         const uint32_t s = sw[i];
-        zrow += (uint32_t)__popc(~px[i] & 0x01010101u);
+        zrow = __dp4a(~px[i] & 0x01010101u, 0x01010101u, zrow);   // slot pixels: LSB 0 (FMA pipe)
         px[i] ^= s & 0xFEFEFEFEu;                       // bits 7..1 decrypted, LSB = map l
         const uint32_t x = (s & 0x01010101u) * 0x10204080u;
         if (i >= 8) ahi = push_nibble(ahi, x);
