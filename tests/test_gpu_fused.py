@@ -90,7 +90,8 @@ def test_fused_shapes(rd, shape, variant):
 
 
 @pytest.mark.parametrize("variant", [oracle.EMR, oracle.LMR, oracle.EMR_MED, oracle.LMR_MED])
-@pytest.mark.parametrize("kw", [dict(rot_enable=0), dict(rot_lmin=3), dict(b=3), dict(b=6)])
+@pytest.mark.parametrize("kw", [dict(rot_enable=0), dict(rot_lmin=2), dict(rot_lmin=3), dict(rot_lmin=4), dict(b=3),
+                                dict(b=6)])
 def test_fused_parameters(rd, variant, kw):
     img = synth.synth_image(256, 320, 5, noise_sigma=2.0)
     _fused(rd, img, variant, 19, **kw)
