@@ -114,6 +114,10 @@ class CudaExecutor:
         self.slots = streams
         self.pool = pool if pool is not None else PinnedPool()
         self.state = state if state is not None else DeviceState()
+        # per stream and kind, the device arena of its last batch, reused while large enough
+        # (a stream takes a new batch only after the previous one completed); each holds at
+        # most twice the largest batch that stream has run
+        self._arenas: dict = {}
 
     def state_bytes(self) -> int:
         return self.state.bytes
@@ -145,15 +149,14 @@ class CudaExecutor:
         bt.event.synchronize()
 
     def results(self, bt: _Batch) -> list[dict]:
-        infos = rd.read_info(bt.hinfo)
-        self.pool.give(bt.hinfo)
-        bt.hinfo = None
-        # the plans' workspace error words came down with the results: a device-side
-        # failure (timeout, index check) fails the whole batch; ECAPACITY is a
+        n = len(bt.outs)
+        infos = rd.read_info(bt.hinfo[: n * rd.INFO_BYTES].view(n, rd.INFO_BYTES))
+        # the plans' workspace error words came down behind the infos, in the same copy: a
+        # device-side failure (timeout, index check) fails the whole batch; ECAPACITY is a
         # per-request outcome
-        codes = bt.hcodes.tolist()
-        self.pool.give(bt.hcodes)
-        bt.hcodes = None
+        codes = bt.hinfo[n * rd.INFO_BYTES:].view(torch.int32)[: bt.hcodes].tolist()
+        self.pool.give(bt.hinfo)
+        bt.hinfo, bt.hcodes = None, None
         for code in codes:
             if code not in (0, rd.RDHEI_ECAPACITY):
                 for o in bt.outs:
@@ -161,13 +164,15 @@ class CudaExecutor:
                 raise rd.RdheiError(f"device reported {rd.STATUS.get(code, code)}")
         return [{**o, "info": inf} for o, inf in zip(bt.outs, infos)]
 
-    def _error_words(self, *plans) -> torch.Tensor:
-        """Pinned copies of the plans' error words, read once the batch's event fired."""
-        h = self.pool.take((4 * len(plans),)).view(torch.int32)
-        st = torch.cuda.current_stream()
+    def _infos_down(self, bt: _Batch, info_err: torch.Tensor, n: int, plans, st):
+        """The plans' error words into the device words behind the n infos, then one copy
+        of both into pinned memory, read once the batch's event fired."""
+        err = info_err[n * rd.INFO_BYTES:].view(torch.int32)
         for i, pl in enumerate(plans):
-            pl.copy_status(h[i:i + 1], st)
-        return h
+            pl.copy_status(err[i:i + 1], st)
+        hinfo = self.pool.take((info_err.numel(),))
+        hinfo.copy_(info_err, non_blocking=True)
+        bt.hinfo, bt.hcodes = hinfo, len(plans)
 
     def discard(self, result: dict, drop_state: bool = True):
         """Give back a result's pinned buffers; unless drop_state is False, also its
@@ -190,15 +195,25 @@ class CudaExecutor:
     def _plan(self, jobs, st):
         return rd.Plan(jobs, st, staging=lambda nb: self.pool.take((nb,)))
 
-    def _arena(self, sizes, zero: bool, dev):
-        """One device allocation cut into 256-byte-aligned pieces of the given sizes
-        (None for a size of None); zero-filled when the kernels OR into it."""
+    def _arena(self, sizes, zero: bool, dev, key=None):
+        """Device memory cut into 256-byte-aligned pieces of the given sizes (None for a
+        size of None), zero-filled when the kernels OR into it.  With a key, the arena of
+        the key's previous batch is reused when large enough, else replaced by one of the
+        next power-of-two size."""
         offs, tot = [], 0
         for n in sizes:
             offs.append(None if n is None else tot)
             if n is not None:
                 tot += (int(n) + 255) & ~255
-        buf = (torch.zeros if zero else torch.empty)(max(tot, 256), dtype=torch.uint8, device=dev)
+        tot = max(tot, 256)
+        buf = self._arenas.get(key) if key is not None else None
+        if buf is None or buf.numel() < tot:
+            size = 1 << (tot - 1).bit_length() if key is not None else tot
+            buf = torch.empty(size, dtype=torch.uint8, device=dev)
+            if key is not None:
+                self._arenas[key] = buf
+        if zero:
+            buf[:tot].zero_()
         return buf, [None if o is None else buf[o:o + int(n)] for o, n in zip(offs, sizes)]
 
     @staticmethod
@@ -210,15 +225,16 @@ class CudaExecutor:
         n = len(reqs)
         px = [r.pixels for r in reqs]
         lmr = [(r.params.variant & 1) == rd.LMR for r in reqs]
-        img_arena, views = self._arena(px * (2 if self.fused else 3), False, dev)
+        img_arena, views = self._arena(px * (2 if self.fused else 3), False, dev, (st.cuda_stream, "img"))
         imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
         marked = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
         enc = [v.view(*r.image.shape) for v, r in zip(views[2 * n:], reqs)]     # separable calls only
         keep = [l and r.keep_state for l, r in zip(lmr, reqs)]
         bit_arena, bviews = self._arena([self._words(p) if l and not k else None for p, l, k in zip(px, lmr, keep)]
-                                        * 2 + [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
+                                        * 2 + [self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES + 16], True,
+                                        dev, (st.cuda_stream, "bits"))
         maps, etas, pays = bviews[:n], bviews[n:2 * n], bviews[2 * n:3 * n]
-        info = bviews[-1].view(n, rd.INFO_BYTES)
+        info = bviews[-1][: n * rd.INFO_BYTES].view(n, rd.INFO_BYTES)
         # maps that stay on the device get an allocation of their own (the store holds it)
         kept = {}
         for i, r in enumerate(reqs):
@@ -257,12 +273,10 @@ class CudaExecutor:
                 he.copy_(etas[i], non_blocking=True)
                 o.update(map_bits=hm, eta_bits=he)
             outs.append(o)
-        hinfo = self.pool.take(tuple(info.shape))
-        hinfo.copy_(info, non_blocking=True)
-        bt.hcodes = self._error_words(*[pl for pl, _ in plans])
+        self._infos_down(bt, bviews[-1], n, [pl for pl, _ in plans], st)
         bt.keep += [img_arena, bit_arena]
         bt.plans = [pl for pl, _ in plans]
-        bt.outs, bt.hinfo = outs, hinfo
+        bt.outs = outs
 
     def _launch_decode(self, bt, reqs, st, dev):
         n = len(reqs)
@@ -275,7 +289,7 @@ class CudaExecutor:
         img_arena, views = self._arena(px * 2 + [r.lmr_map.numel() if r.lmr_map is not None and h is None else None
                                                  for r, h in zip(reqs, held)]
                                        + [r.lmr_eta.numel() if r.lmr_eta is not None and h is None else None
-                                          for r, h in zip(reqs, held)], False, dev)
+                                          for r, h in zip(reqs, held)], False, dev, (st.cuda_stream, "img"))
         imgs = [v.view(*r.image.shape) for v, r in zip(views[:n], reqs)]
         rec = [v.view(*r.image.shape) for v, r in zip(views[n:2 * n], reqs)]
         maps, etas = views[2 * n:3 * n], views[3 * n:]
@@ -285,8 +299,9 @@ class CudaExecutor:
                 maps[i], etas[i] = h[:w], h[w:]
                 h.record_stream(st)                 # allocated on the encode's stream, read on this one
                 bt.keep.append(h)                   # alive until the batch completes, even if evicted
-        bit_arena, bviews = self._arena([self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES], True, dev)
-        bits, info = bviews[:n], bviews[-1].view(n, rd.INFO_BYTES)
+        bit_arena, bviews = self._arena([self._words(r.nbits) for r in reqs] + [n * rd.INFO_BYTES + 16], True, dev,
+                                        (st.cuda_stream, "bits"))
+        bits, info = bviews[:n], bviews[-1][: n * rd.INFO_BYTES].view(n, rd.INFO_BYTES)
         if self.fused:
             jf = [rd.make_job(r.params, *r.image.shape, src=imgs[i], dst=rec[i], map_bits=maps[i], eta_bits=etas[i],
                               bits_out=bits[i], max_bits=r.nbits, info=info[i], b=r.b) for i, r in enumerate(reqs)]
@@ -311,12 +326,10 @@ class CudaExecutor:
             hb.copy_(bits[i], non_blocking=True)
             hr.copy_(rec[i], non_blocking=True)
             outs.append({"bits": hb, "recovered": hr})
-        hinfo = self.pool.take(tuple(info.shape))
-        hinfo.copy_(info, non_blocking=True)
-        bt.hcodes = self._error_words(*[pl for pl, _ in plans])
+        self._infos_down(bt, bviews[-1], n, [pl for pl, _ in plans], st)
         bt.keep += [img_arena, bit_arena]
         bt.plans = [pl for pl, _ in plans]
-        bt.outs, bt.hinfo = outs, hinfo
+        bt.outs = outs
 
 
 class Server(Scheduler):
