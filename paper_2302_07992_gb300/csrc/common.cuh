@@ -298,9 +298,10 @@ __host__ __device__ __forceinline__ uint32_t rot_bits(uint32_t lut, uint32_t a, 
 
 // Up to 32 bits of an MSB-first stream starting at bit `pos`, returned LSB-first
 // (bit c = stream bit pos + c); `nwords` bounds the 32-bit words that may be read.
-__device__ __forceinline__ uint32_t stream_bits32(const uint8_t* s, uint64_t nwords, uint64_t pos) {
+// 32-bit positions: an image holds at most 2^27 pixels, its streams at most 2^30 bits.
+__device__ __forceinline__ uint32_t stream_bits32(const uint8_t* s, uint32_t nwords, uint32_t pos) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(s);
-  uint64_t wi = pos >> 5;
+  const uint32_t wi = pos >> 5;
   uint32_t sh = (uint32_t)(pos & 31);
   uint32_t w0 = wi < nwords ? bswap32(__ldg(w + wi)) : 0u;
   uint32_t w1 = (sh && wi + 1 < nwords) ? bswap32(__ldg(w + wi + 1)) : 0u;
@@ -310,9 +311,9 @@ __device__ __forceinline__ uint32_t stream_bits32(const uint8_t* s, uint64_t nwo
 
 // The same from a stream that the calling kernel itself wrote earlier (coherent
 // L2 loads: the read-only path may not be used for data written by the same kernel).
-__device__ __forceinline__ uint32_t stream_bits32_cg(const uint8_t* s, uint64_t nwords, uint64_t pos) {
+__device__ __forceinline__ uint32_t stream_bits32_cg(const uint8_t* s, uint32_t nwords, uint32_t pos) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(s);
-  uint64_t wi = pos >> 5;
+  const uint32_t wi = pos >> 5;
   uint32_t sh = (uint32_t)(pos & 31);
   uint32_t w0 = wi < nwords ? bswap32(__ldcg(w + wi)) : 0u;
   uint32_t w1 = (sh && wi + 1 < nwords) ? bswap32(__ldcg(w + wi + 1)) : 0u;

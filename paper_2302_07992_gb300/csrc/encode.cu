@@ -428,7 +428,7 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
           }
         }
         const bool plain = (W & 15) == 0;
-        const uint64_t pos = (uint64_t)off;
+        const uint32_t pos = (uint32_t)off;                         // < 2^27: 32-bit stream positions
         uint32_t e[4];
         if (!LMR) {
 #pragma unroll
@@ -438,7 +438,7 @@ __device__ __forceinline__ void enc_rows_body(const Batch& B, uint32_t strip, ui
 #pragma unroll
           for (int i = 0; i < 4; i++) e[i] = v[i] ^ s[i];
           if (pos < d.side_nbits && d.side_bits) {
-            const uint64_t nws = (d.side_nbits + 31) >> 5;
+            const uint32_t nws = (uint32_t)((d.side_nbits + 31) >> 5);
             const uint32_t sb = stream_bits32(d.side_bits, nws, pos);    // bit c = side bit pos + c
             const int nside = (int)umin64((uint64_t)valid, d.side_nbits - pos);
 #pragma unroll

@@ -457,7 +457,7 @@ __global__ void k_lmr_side(Batch B) {
   const uint64_t p0 = (uint64_t)(g - d.chunk_base) * CHUNK_PX + (uint64_t)HIDE_PX * threadIdx.x;
   if (p0 >= N || p0 >= d.side_nbits || !d.side_bits) return;
   const int n = (int)umin64(umin64(HIDE_PX, N - p0), d.side_nbits - p0);
-  const uint32_t sb = stream_bits32(d.side_bits, (d.side_nbits + 31) >> 5, p0);
+  const uint32_t sb = stream_bits32(d.side_bits, (uint32_t)((d.side_nbits + 31) >> 5), (uint32_t)p0);
   for (int k = 0; k < n; k++) d.dst[p0 + k] = (uint8_t)((d.dst[p0 + k] & 0x7Fu) | (((sb >> k) & 1u) << 7));
 }
 

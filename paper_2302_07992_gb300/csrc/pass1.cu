@@ -287,11 +287,11 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
       auxbits = ((uint64_t)ahi << 32) | alo;
       zrow -= (uint32_t)(64 - len);                     // bytes past the row end were loaded as 0
     } else {
-      const uint64_t nw = ((uint64_t)H * W + 31) >> 5;
-      uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, base) : 0u;
-      uint32_t lb1 = len > 32 ? stream_bits32(d.map_bits, nw, base + 32) : 0u;
-      uint32_t eb0 = len > 0 ? stream_bits32(d.eta_bits, nw, base) : 0u;
-      uint32_t eb1 = len > 32 ? stream_bits32(d.eta_bits, nw, base + 32) : 0u;
+      const uint32_t nw = ((uint32_t)H * (uint32_t)W + 31) >> 5, pb = (uint32_t)base;
+      uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, pb) : 0u;
+      uint32_t lb1 = len > 32 ? stream_bits32(d.map_bits, nw, pb + 32) : 0u;
+      uint32_t eb0 = len > 0 ? stream_bits32(d.eta_bits, nw, pb) : 0u;
+      uint32_t eb1 = len > 32 ? stream_bits32(d.eta_bits, nw, pb + 32) : 0u;
       uint64_t lb = ((uint64_t)lb1 << 32) | lb0, eb = ((uint64_t)eb1 << 32) | eb0;
 #pragma unroll
       for (int i = 0; i < 16; i++) {

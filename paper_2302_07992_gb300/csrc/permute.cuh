@@ -170,7 +170,7 @@ __device__ __forceinline__ uint32_t flags16(const uint32_t w[4], int bit) {
 // Write `n` (<= 16) MSB-first bits v16 (bit 15 first) at stream bit `pos`.  `plain`:
 // the caller guarantees pos % 16 == 0 and n == 16 for every chunk of the stream (a
 // plain 16-bit store); otherwise bits are OR-ed into words the launcher zeroed.
-__device__ __forceinline__ void put_bits16(uint8_t* stream, uint64_t pos, uint32_t v16, int n, bool plain) {
+__device__ __forceinline__ void put_bits16(uint8_t* stream, uint32_t pos, uint32_t v16, int n, bool plain) {
   if (n <= 0) return;
   if (plain) {
     *reinterpret_cast<uint16_t*>(stream + (pos >> 3)) = (uint16_t)(((v16 >> 8) & 0xFFu) | ((v16 & 0xFFu) << 8));
@@ -178,8 +178,8 @@ __device__ __forceinline__ void put_bits16(uint8_t* stream, uint64_t pos, uint32
   }
   v16 &= (0xFFFFu << (16 - n)) & 0xFFFFu;
   uint32_t* w = reinterpret_cast<uint32_t*>(stream);
-  uint64_t wi = pos >> 5;
-  uint32_t sh = (uint32_t)(pos & 31);
+  const uint32_t wi = pos >> 5;
+  const uint32_t sh = pos & 31;
   uint64_t run = ((uint64_t)v16 << 48) >> sh;              // bit 63 = word wi's first bit
   uint32_t hi = (uint32_t)(run >> 32), lo = (uint32_t)run;
   if (hi) atomicOr(w + wi, bswap32(hi));

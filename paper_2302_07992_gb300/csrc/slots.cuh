@@ -67,7 +67,7 @@ __device__ __forceinline__ void issue_chunk(const ImgDesc& d, uint32_t c, int t,
         if (k < r.valid) r.px[k >> 2] |= (uint32_t)src[k] << (8 * (k & 3));
     }
   }
-  if (lmr && r.valid > 0) r.lbits = stream_bits32(d.map_bits, (N + 31) >> 5, p0);
+  if (lmr && r.valid > 0) r.lbits = stream_bits32(d.map_bits, (uint32_t)((N + 31) >> 5), (uint32_t)p0);
 }
 
 __device__ __forceinline__ uint32_t zero_mask(const ImgDesc& d, const ChunkPx& r) {
@@ -173,7 +173,8 @@ __device__ __forceinline__ void load_run(const ImgDesc& d, const uint8_t* img, u
   }
   if (d.variant == RDHEI_LMR && r.valid > 0) {
     const uint64_t nw = ((uint64_t)d.H * d.W + 31) >> 5;
-    r.lbits = coherent ? stream_bits32_cg(d.map_bits, nw, q0) : stream_bits32(d.map_bits, nw, q0);
+    r.lbits = coherent ? stream_bits32_cg(d.map_bits, (uint32_t)nw, (uint32_t)q0)
+                       : stream_bits32(d.map_bits, (uint32_t)nw, (uint32_t)q0);
   }
 }
 
@@ -200,7 +201,8 @@ __device__ __forceinline__ void load_strip_run(const ImgDesc& d, const uint8_t* 
   }
   if (d.variant == RDHEI_LMR && r.valid > 0) {
     const uint64_t nw = ((uint64_t)d.H * d.W + 31) >> 5;
-    r.lbits = COHERENT ? stream_bits32_cg(d.map_bits, nw, p0 + q0) : stream_bits32(d.map_bits, nw, p0 + q0);
+    const uint32_t pos = (uint32_t)p0 + q0;
+    r.lbits = COHERENT ? stream_bits32_cg(d.map_bits, (uint32_t)nw, pos) : stream_bits32(d.map_bits, (uint32_t)nw, pos);
   }
 }
 
