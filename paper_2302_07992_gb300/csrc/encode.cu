@@ -505,10 +505,13 @@ __device__ __forceinline__ void stage_message(const ImgDesc& d, uint64_t w_lo, u
     uint32_t o[16];
     const uint64_t j = j0 + t;
     chacha20_block<2>(d.k2, (uint32_t)j, d.n2, o, d.one);
+    // word i of the block is window word 16 t + i - o0, o0 = w_lo's offset in block j0
+    const uint32_t o0 = (uint32_t)(w_lo & 15);
+    const uint32_t* pj = pay + 16 * j;
 #pragma unroll
     for (int i = 0; i < 16; i++) {
-      const uint64_t w = 16 * j + i;
-      if (w >= w_lo && w < w_lo + nw) buf[w - w_lo] = bswap32(__ldg(pay + w) ^ o[i]);
+      const uint32_t k = 16u * (uint32_t)t + (uint32_t)i - o0;      // wraps (large) before the window
+      if (k < nw) buf[k] = bswap32(__ldg(pj + i) ^ o[i]);
     }
   }
   if (t == 0) buf[nw] = 0u;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
   const int y = ty * TILE + r, x0 = tx * TILE;
   const bool row_ok = y < H;
   const int len = row_ok ? min(TILE, W - x0) : 0;
-  const uint64_t base = (uint64_t)y * W + x0;
+  const uint32_t base = (uint32_t)y * (uint32_t)W + (uint32_t)x0;   // < 2^28: 32-bit positions
 
   for (int i = r; i < SUBTREE_BYTES / 4; i += 64) reinterpret_cast<uint32_t*>(sub)[i] = 0u;
 
@@ -107,11 +107,11 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
 #pragma unroll
     for (int i = 0; i < 16; i++) sw[i] = 0u;
   } else if (aligned || !GENERAL) {
-    chacha20_block<2>(d.k1, (uint32_t)(base >> 6), d.n1, sw, d.one);
+    chacha20_block<2>(d.k1, base >> 6, d.n1, sw, d.one);
   } else {
     // the row straddles two ChaCha blocks: stage both and pick the 64 bytes
     uint32_t o[16];
-    const uint64_t b0 = base >> 6;
+    const uint32_t b0 = base >> 6;
     const int off = (int)(base & 63);
     if (len > 0) {
       chacha20_block<2>(d.k1, (uint32_t)b0, d.n1, o, d.one);
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(64, 20) k_pass1(Batch B) {
       auxbits = ((uint64_t)ahi << 32) | alo;
       zrow -= (uint32_t)(64 - len);                     // bytes past the row end were loaded as 0
     } else {
-      const uint32_t nw = ((uint32_t)H * (uint32_t)W + 31) >> 5, pb = (uint32_t)base;
+      const uint32_t nw = ((uint32_t)H * (uint32_t)W + 31) >> 5, pb = base;
       uint32_t lb0 = len > 0 ? stream_bits32(d.map_bits, nw, pb) : 0u;
       uint32_t lb1 = len > 32 ? stream_bits32(d.map_bits, nw, pb + 32) : 0u;
       uint32_t eb0 = len > 0 ? stream_bits32(d.eta_bits, nw, pb) : 0u;
