@@ -284,7 +284,10 @@ __device__ __forceinline__ uint32_t z2_window(uint64_t j0, uint64_t send) {
   return (uint32_t)umin64(Z2_WINDOW_BLOCKS, (((send - 1) >> 5) >> 4) - j0 + 1);
 }
 
-__global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
+// Five CTAs per SM (48 registers) with each chunk's loads at the top of its iteration
+// measured faster than four (64 registers) with the next chunk's loads in flight during
+// the current one: 0.231 -> 0.219 ms on 1000 x 512^2.
+__global__ void __launch_bounds__(HIDE_THREADS, 5) k_extract_strips(Batch B) {
   pdl_wait();      // the previous kernel of the operation has finished
   pdl_trigger();
   __shared__ uint32_t sbuf[SBUF_WORDS];
@@ -324,17 +327,15 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
   const uint8_t* const ssrc = d.src + p0;
   const uint32_t npx = (uint32_t)(p1 - p0), send_r = (uint32_t)(send - 32 * W0);
   uint32_t* const outp = out + W0;
-  ChunkPx cur;
-  load_strip_run<false>(d, ssrc, p0, (uint32_t)HIDE_PX * t, npx, cur);
-  // the part's first keystream window, while the first chunk's loads are in flight
+  // the part's first keystream window
   uint32_t jb = 0;                                           // window: blocks [J0 + jb, J0 + jb + Jn)
   uint32_t Jn = z2_window(J0, send);
   z2_blocks(d, J0, Jn, z2buf);
   __syncthreads();   // tables, keystream
   uint32_t g = (uint32_t)(G0 & 31);
   for (uint32_t c0 = 0; c0 < npx && g < send_r; c0 += SCAN_PX) {
-    ChunkPx nxt;                                             // next chunk in flight
-    load_strip_run<false>(d, ssrc, p0, c0 + SCAN_PX + (uint32_t)HIDE_PX * t, npx, nxt);
+    ChunkPx cur;
+    load_strip_run<false>(d, ssrc, p0, c0 + (uint32_t)HIDE_PX * t, npx, cur);
     const uint32_t zmask = zero_mask(d, cur);
     uint32_t Tc;
     const uint32_t my_off = block_exclusive_scan((uint32_t)__popc(zmask) * slots, warp_tot, Tc);
@@ -379,7 +380,6 @@ __global__ void __launch_bounds__(HIDE_THREADS, 4) k_extract_strips(Batch B) {
       }
     }
     g += Tc;
-    cur = nxt;
   }
 }
 
